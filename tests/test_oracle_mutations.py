@@ -1,0 +1,130 @@
+"""Planted mistakes in the oracle must each break at least one pin.
+
+Each case patches one plausible error into oracle.gpe_oracle (on the CPU) and
+re-runs the quick pins from test_oracle_pins; the test passes only if some pin
+now fails.  This checks that the pins constrain every part of the oracle.
+"""
+import contextlib
+
+import numpy as np
+import pytest
+
+from oracle import gpe_oracle as O
+
+import test_oracle_pins as P
+
+QUICK_PINS = [
+    lambda: P.test_P0_spectral_derivative_of_single_mode(0),
+    P.test_P1_harmonic_gaussian_2d,
+    P.test_P2_angular_momentum_sign_and_scale,
+    lambda: P.test_P3_hamiltonian_hermitian((16, 16)),
+    P.test_P4_gradient_is_two_H_phi,
+    P.test_P5_exact_energy_change_along_geodesic,
+    P.test_P5_curvature_matches_second_difference,
+    lambda: P.test_P6_preconditioner_hermitian_positive((16, 16)),
+    P.test_P6_kinetic_preconditioner_inverts_shifted_laplacian,
+]
+
+
+def pins_all_pass():
+    for pin in QUICK_PINS:
+        try:
+            pin()
+        except AssertionError:
+            return False
+    return True
+
+
+@contextlib.contextmanager
+def patched(name, fn):
+    old = getattr(O, name)
+    setattr(O, name, fn)
+    try:
+        yield
+    finally:
+        setattr(O, name, old)
+
+
+def _lz_wrong_sign(prob, f):
+    x, y = prob.coord(0), prob.coord(1)
+    return 1j * (x * O.d1_axis(prob, f, 1) - y * O.d1_axis(prob, f, 0))
+
+
+def _lz_swapped_axes(prob, f):
+    x, y = prob.coord(0), prob.coord(1)
+    return -1j * (x * O.d1_axis(prob, f, 0) - y * O.d1_axis(prob, f, 1))
+
+
+def _inner_unweighted(prob, f, g):
+    return np.vdot(f, g)
+
+
+_orig_apply_H = O.apply_H
+_orig_freq = O.Problem.freq
+
+
+def _H_without_nonlinearity(prob, phi, f):
+    return O.apply_A(prob, f)
+
+
+def _H_with_half_nonlinearity(prob, phi, f):
+    return O.apply_A(prob, f) + 0.5 * prob.eta * np.abs(phi) ** 2 * f
+
+
+def _hessian_as_printed(prob, phi, f):
+    # the formula exactly as printed: <f, H f> + eta Re <phi^2, f^2>
+    w = prob.weight
+    return (O.inner(prob, f, _orig_apply_H(prob, phi, f)).real
+            + prob.eta * w * np.sum(np.conj(phi) ** 2 * f ** 2).real)
+
+
+_orig_delta = O.delta_energy
+
+
+def _delta_wrong_coefficient(m, eta, theta):
+    c, s = np.cos(theta), np.sin(theta)
+    return _orig_delta(m, eta, theta) - 0.5 * eta * 2.0 * c * s ** 3 * (m["VW"] - m["U1"])
+
+
+def _precond_nonsymmetric(prob, phi, r, alpha):
+    return O.precond_V(prob, phi, alpha) * O.precond_delta(prob, r, alpha)
+
+
+def _delta_shift_wrong(prob, f, alpha):
+    return O.dftn(prob, O.dftn(prob, f) / (alpha + 2.0 * O.kinetic_symbol(prob)), inverse=True)
+
+
+def _freq_twice(self, i):
+    return 2.0 * _orig_freq(self, i)
+
+
+MUTATIONS = {
+    "Lz_sign": ("Lz", _lz_wrong_sign),
+    "Lz_axes": ("Lz", _lz_swapped_axes),
+    "no_weight": ("inner", _inner_unweighted),
+    "H_no_eta": ("apply_H", _H_without_nonlinearity),
+    "H_half_eta": ("apply_H", _H_with_half_nonlinearity),
+    "hessian_as_printed": ("hessian_form", _hessian_as_printed),
+    "deltaE_coeff": ("delta_energy", _delta_wrong_coefficient),
+    "P_nonsymmetric": ("precond_C", _precond_nonsymmetric),
+    "P_delta_shift": ("precond_delta", _delta_shift_wrong),
+}
+
+
+def test_unmutated_oracle_passes_quick_pins():
+    assert pins_all_pass()
+
+
+@pytest.mark.parametrize("case", sorted(MUTATIONS))
+def test_mutation_is_caught(case):
+    name, fn = MUTATIONS[case]
+    with patched(name, fn):
+        assert not pins_all_pass(), f"planted mistake {case} passed every pin"
+
+
+def test_frequency_scale_mutation_is_caught():
+    O.Problem.freq = _freq_twice
+    try:
+        assert not pins_all_pass()
+    finally:
+        O.Problem.freq = _orig_freq

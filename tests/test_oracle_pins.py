@@ -1,0 +1,258 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(not by the oracle itself).  Each test names the pin it implements:
+
+P0 transforms = brute-force DFT sums; P1 harmonic ground state (closed form);
+P2 sign/scale of L_z via phi_b; P3 Hermiticity; P4 gradient = 2 H phi (FD);
+P5 exact energy change along the geodesic and its curvature (FD);
+P6 preconditioner symmetry/positivity and exact inversion of P_Delta;
+P7 converged energies printed in the paper's Table 2;
+P8 method invariants (monotone energy, unit norm); P9 stationarity.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gpe_oracle as O
+from paper_1611_02045_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_energies.json")
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def prob2(M=16, L=4.0, eta=3.0, omega=0.4, backend="fft", V=None, n=None):
+    n = n or (M, M)
+    L_ = (L,) * len(n)
+    if V is None:
+        V = I.harmonic(n, L_)
+    return O.Problem(n, L_, eta, omega, V, backend=backend)
+
+
+# ---------------------------------------------------------------- P0
+@pytest.mark.parametrize("n", [(8, 8), (4, 8), (4, 4, 4), (8, 4, 2)])
+def test_P0_separable_dft_equals_bruteforce(n):
+    """Naive separable DFT == the d-dimensional DFT sum written out over all
+    (p, k) pairs (Section 3 convention)."""
+    f = I.random_field(11, n, (1.0,) * len(n))
+    p = O.Problem(n, (1.0,) * len(n), 0.0, 0.0, np.zeros(f.shape), backend="naive")
+    shape = f.shape  # [z][y][x]
+    idx = np.array(np.unravel_index(np.arange(f.size), shape)).T  # (N, d) numpy axes
+    Ms = np.array(shape)
+    phase = -2j * np.pi * (idx[:, None, :] * idx[None, :, :] / Ms).sum(-1)
+    brute = (np.exp(phase) @ f.ravel()).reshape(shape)
+    assert rel(O.dftn(p, f), brute) < 1e-13
+    back = (np.exp(-phase) @ brute.ravel()).reshape(shape) / f.size
+    assert rel(O.dftn(p, brute, inverse=True), back) < 1e-13
+    assert rel(back, f) < 1e-13
+
+
+def test_P0_fft_backend_equals_naive_backend():
+    n = (16, 8)
+    V = I.harmonic(n, (3.0, 3.0))
+    pf = O.Problem(n, (3.0, 3.0), 2.0, 0.7, V, backend="fft")
+    pn = O.Problem(n, (3.0, 3.0), 2.0, 0.7, V, backend="naive")
+    phi = I.random_field(1, n, (3.0, 3.0))
+    f = I.random_field(2, n, (3.0, 3.0))
+    assert rel(O.apply_H(pf, phi, f), O.apply_H(pn, phi, f)) < 1e-13
+    assert rel(O.precond_C(pf, phi, f, 2.5), O.precond_C(pn, phi, f, 2.5)) < 1e-13
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_P0_spectral_derivative_of_single_mode(axis):
+    """A single Fourier mode e^{i xi_p (x+L)} has d/dx = i xi_p, d2/dx2 = -xi_p^2,
+    with xi_p = p pi / L (Section 3), including the kept Nyquist mode p = -M/2."""
+    n, L = (16, 16), (2.5, 2.5)
+    p = O.Problem(n, L, 0.0, 0.0, np.zeros((16, 16)))
+    x = p.coord(axis) + L[axis]
+    for q in (1, 3, -5, -8):
+        xi = q * np.pi / L[axis]
+        f = np.exp(1j * xi * x) * np.ones((16, 16))
+        assert rel(O.d1_axis(p, f, axis), 1j * xi * f) < 1e-12
+        assert rel(O.d2_axis(p, f, axis), -xi * xi * f) < 1e-12
+
+
+# ---------------------------------------------------------------- P1
+def test_P1_harmonic_gaussian_2d():
+    n, L = (64, 64), (8.0, 8.0)
+    p = O.Problem(n, L, 0.0, 0.0, I.harmonic(n, L))
+    g = I.phi_a(n, L)
+    assert abs(O.norm(p, g) - 1.0) < 1e-13
+    e = O.energy_parts(p, g)
+    assert abs(e["total"] - 1.0) < 1e-12
+    assert abs(e["kin"] - 0.5) < 1e-12 and abs(e["pot"] - 0.5) < 1e-12  # virial split
+    assert np.max(np.abs(O.apply_H(p, g, g) - g)) < 1e-12
+
+
+def test_P1_harmonic_gaussian_3d_anisotropic():
+    n, L = (64, 64, 64), (8.0, 8.0, 8.0)  # h = 1/4: aliasing of the Gaussians below 1e-15
+    p = O.Problem(n, L, 0.0, 0.0, I.harmonic(n, L, [1.0, 1.0, 2.0]))
+    g = I.anisotropic_gaussian(n, L, [1.0, 1.0, 2.0])
+    assert abs(O.energy(p, g) - 2.0) < 1e-12
+    assert abs(O.chemical_potential(p, g) - 2.0) < 1e-12
+
+
+def test_P1_pcg_converges_to_harmonic_ground_state():
+    n, L = (32, 32), (8.0, 8.0)
+    p = O.Problem(n, L, 0.0, 0.0, I.harmonic(n, L))
+    phi0 = I.perturbed(I.phi_a(n, L), 7, n, L, amp=0.2)
+    phi, rep = O.pcg_solve(p, phi0, O.SolveOptions(tol_res_inf=1e-10, max_iter=500))
+    assert rep["status"] == "converged"
+    assert abs(rep["E"] - 1.0) < 1e-12
+    assert abs(rep["lam"] - 1.0) < 1e-9
+
+
+# ---------------------------------------------------------------- P2
+def test_P2_angular_momentum_sign_and_scale():
+    """L_z phi_a = 0 (radial), L_z phi_b = +phi_b for phi_b = (x+iy) phi_a; at eta = 0
+    H phi_b = (2 - omega) phi_b and E(phi_b) = 2 - omega (Section 2, initial data (b))."""
+    n, L = (64, 64), (8.0, 8.0)
+    om = 0.3
+    p = O.Problem(n, L, 0.0, om, I.harmonic(n, L))
+    a = I.phi_a(n, L)
+    b = I.normalise(I.phi_b(n, L), n, L)
+    assert np.max(np.abs(O.Lz(p, a))) < 1e-12
+    assert np.max(np.abs(O.Lz(p, b) - b)) < 1e-11
+    assert np.max(np.abs(O.apply_H(p, b, b) - (2.0 - om) * b)) < 1e-11
+    assert abs(O.energy(p, b) - (2.0 - om)) < 1e-12
+    assert abs(O.energy(p, np.conj(b)) - (2.0 + om)) < 1e-12
+
+
+# ---------------------------------------------------------------- P3
+@pytest.mark.parametrize("n", [(16, 16), (8, 16, 8)])
+def test_P3_hamiltonian_hermitian(n):
+    L = (3.0,) * len(n)
+    p = O.Problem(n, L, 5.0, 0.8, I.harmonic(n, L))
+    phi, f, g = (I.random_field(s, n, L) for s in (1, 2, 3))
+    lhs = O.inner(p, g, O.apply_H(p, phi, f))
+    rhs = np.conj(O.inner(p, f, O.apply_H(p, phi, g)))
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+# ---------------------------------------------------------------- P4
+def test_P4_gradient_is_two_H_phi():
+    n, L = (16, 16), (4.0, 4.0)
+    p = O.Problem(n, L, 7.0, 0.6, I.harmonic(n, L))
+    phi = I.normalise(I.phi_d(n, L, 0.6) * (1 + 0.1 * I.random_field(4, n, L)), n, L)
+    d = I.random_field(5, n, L) * 0.1
+    eps = 1e-5
+    fd = (O.energy(p, phi + eps * d) - O.energy(p, phi - eps * d)) / (2 * eps)
+    an = 2.0 * O.inner(p, O.apply_H(p, phi, phi), d).real
+    assert abs(fd - an) < 1e-8 * abs(an)
+
+
+# ---------------------------------------------------------------- P5
+def _tangent_unit(p, phi, seed):
+    q = I.random_field(seed, p.n, p.L)
+    q = q - O.inner(p, q, phi).real * phi
+    return q / O.norm(p, q)
+
+
+def test_P5_exact_energy_change_along_geodesic():
+    n, L = (16, 16), (4.0, 4.0)
+    p = O.Problem(n, L, 40.0, 0.7, I.harmonic(n, L))
+    phi = I.normalise(I.phi_d(n, L, 0.7), n, L)
+    q = _tangent_unit(p, phi, 9)
+    Hphi = O.apply_H(p, phi, phi)
+    lam = O.inner(p, phi, Hphi).real
+    m = O.step_moments(p, phi, Hphi, lam, q)
+    E0 = O.energy(p, phi)
+    for th in (1e-3, 1e-2, 0.1, 0.5, 1.3, -0.4):
+        direct = O.energy(p, np.cos(th) * phi + np.sin(th) * q) - E0
+        model = O.delta_energy(m, p.eta, th)
+        assert abs(direct - model) < 1e-12 * abs(E0) + 1e-11 * abs(direct)
+
+
+def test_P5_curvature_matches_second_difference():
+    n, L = (16, 16), (4.0, 4.0)
+    p = O.Problem(n, L, 40.0, 0.7, I.harmonic(n, L))
+    phi = I.normalise(I.phi_d(n, L, 0.7), n, L)
+    q = _tangent_unit(p, phi, 10)
+    lam = O.chemical_potential(p, phi)
+    Eh = lambda t: O.energy(p, np.cos(t) * phi + np.sin(t) * q)  # noqa: E731
+    h = 1e-3
+    fd2 = (Eh(h) - 2 * Eh(0.0) + Eh(-h)) / (h * h)
+    assert abs(fd2 - 2.0 * O.model_curvature(p, phi, lam, q)) < 1e-5 * abs(fd2)
+    fd1 = (Eh(h) - Eh(-h)) / (2 * h)
+    R = O.inner(p, O.apply_H(p, phi, phi), q).real
+    assert abs(fd1 - 2.0 * R) < 1e-5 * abs(fd1)
+
+
+# ---------------------------------------------------------------- P6
+@pytest.mark.parametrize("n", [(16, 16), (8, 8, 16)])
+def test_P6_preconditioner_hermitian_positive(n):
+    L = (3.0,) * len(n)
+    p = O.Problem(n, L, 5.0, 0.8, I.harmonic(n, L))
+    phi, f, g = (I.random_field(s, n, L) for s in (21, 22, 23))
+    alpha = 1.7
+    a = O.inner(p, g, O.precond_C(p, phi, f, alpha))
+    b = np.conj(O.inner(p, f, O.precond_C(p, phi, g, alpha)))
+    assert abs(a - b) < 1e-13 * abs(a)
+    for s in range(5):
+        h = I.random_field(30 + s, n, L)
+        assert O.inner(p, h, O.precond_C(p, phi, h, alpha)).real > 0
+
+
+def test_P6_kinetic_preconditioner_inverts_shifted_laplacian():
+    n, L = (16, 8), (3.0, 2.0)
+    p = O.Problem(n, L, 0.0, 0.0, np.zeros((8, 16)))
+    f = I.random_field(3, n, L)
+    alpha = 0.9
+    g = O.precond_delta(p, f, alpha)
+    assert rel(alpha * g - 0.5 * O.laplacian(p, g), f) < 1e-13
+    # P_C with V = 0 and eta = 0 is P_Delta / alpha (P_V = 1/alpha)
+    assert rel(O.precond_C(p, np.zeros_like(f), f, alpha), g / alpha) < 1e-13
+
+
+# ---------------------------------------------------------------- P7
+def _paper():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.5])
+def test_P7_radial_state_energy_matches_paper(omega):
+    n, L = (256, 256), (16.0, 16.0)
+    p = O.Problem(n, L, 500.0, omega, I.harmonic(n, L))
+    phi, rep = O.pcg_solve(p, I.phi_a(n, L), O.SolveOptions(tol_res_inf=1e-8, max_iter=300))
+    assert rep["status"] == "converged"
+    assert abs(rep["E"] - _paper()["radial_state_from_phi_a"]["any_omega"]) < 1e-4
+
+
+@pytest.mark.parametrize("omega", ["0.5", "0.6"])
+def test_P7_vortex_state_energy_matches_paper(omega):
+    n, L = (256, 256), (16.0, 16.0)
+    p = O.Problem(n, L, 500.0, float(omega), I.harmonic(n, L))
+    phi, rep = O.pcg_solve(p, I.phi_b(n, L), O.SolveOptions(tol_res_inf=1e-8, max_iter=300))
+    assert rep["status"] == "converged"
+    assert abs(rep["E"] - _paper()["vortex_state_from_phi_b"][omega]) < 1e-4
+
+
+def test_P7_fast_rotation_lowest_energy_matches_paper():
+    """omega = 0.9 from phi_d: the lowest energy 4.7777 of Table 2."""
+    n, L = (256, 256), (16.0, 16.0)
+    p = O.Problem(n, L, 500.0, 0.9, I.harmonic(n, L))
+    phi, rep = O.pcg_solve(p, I.phi_d(n, L, 0.9), O.SolveOptions(tol_res_inf=3e-5, max_iter=4000))
+    assert rep["status"] == "converged"
+    assert abs(rep["E"] - _paper()["lowest_energy"]["0.9"]) < 1e-4
+
+
+# ---------------------------------------------------------------- P8 / P9
+def test_P8_P9_invariants_and_stationarity():
+    w = I.workload("c64_2d")
+    p = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    keep = tuple(range(0, 400, 7))
+    phi, rep = O.pcg_solve(p, w["phi0"], O.SolveOptions(tol_res_inf=1e-8, max_iter=2000), keep_iterates=keep)
+    assert rep["status"] == "converged"
+    E = np.array([e["E"] for e in rep["log"]])
+    assert np.all(np.diff(E) <= 1e-12 * abs(E[0]))  # every accepted step lowers E
+    for ph in rep["iterates"].values():
+        assert abs(O.norm(p, ph) - 1.0) < 1e-13
+    Hphi = O.apply_H(p, phi, phi)
+    lam = O.inner(p, phi, Hphi).real
+    assert np.max(np.abs(Hphi - lam * phi)) < 1e-8
+    # energy error is quadratic in the residual near the minimum
+    assert abs(E[-1] - rep["E"]) == 0.0
