@@ -1,0 +1,335 @@
+"""Benchmark: PCG_C ground states per second on one GB300 (and N replicas).
+
+A step is one complete ground-state solve of the 2D fast-rotation workload
+(256x256 on [-16,16]^2, V = r^2/2, eta = 1000, omega = 0.9, Gaussian-plus-
+vortex initial guess, mixed precision: complex64 phase then complex128
+refinement, stop at ||H phi - lambda phi||_inf < 1e-8), through the C ABI with
+phi already in device memory.  Alongside it the line reports:
+
+  roofline      H phi (the x and y passes of gpe_apply_H, complex64 + f32 V)
+                on a 256x256x512 grid (working set > L2), achieved = 20 B/pt
+                algorithmic bytes / CUDA-event time, vs the measured HBM peak;
+  e2e           the same solve with phi in pinned HOST memory (H2D/D2H copies
+                inside the call and inside the timed region);
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload;
+  secondary     the 128^3 3D workload (eta = 5000, omega = 0.8), ground states/s.
+
+--impl reference runs the CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fast256_2d"
+METRIC = "ground states/sec to residual 1e-8 (256², 128³); H·φ GB/s vs HBM peak"
+UNIT = "ground_states/s"
+HPHI_GRID = (256, 256, 512)
+HPHI_BYTES_PER_PT = 20  # read phi (c64) + V (f32), write H phi (c64)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(seconds=12.0, max_iters=400):
+    """Time FP64 oracle PCG_C iterations on the workload (bounded sample)."""
+    from oracle import gpe_oracle as O
+    from paper_1611_02045_gb300 import inputs as I
+    w = I.workload(WORKLOAD)
+    prob = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    # one iteration first (imports, caches), then grow until the time budget
+    t0 = time.perf_counter()
+    O.pcg_solve(prob, w["phi0"], O.SolveOptions(max_iter=1))
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-3) / 2.0
+    k = int(max(5, min(max_iters, seconds / per)))
+    t0 = time.perf_counter()
+    _, rep = O.pcg_solve(prob, w["phi0"], O.SolveOptions(max_iter=k))
+    dt = time.perf_counter() - t0
+    return dt / max(rep["iters"], 1), rep["iters"]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle (numpy), bounded samples."""
+    if rank != 0:
+        return
+    from oracle import gpe_oracle as O  # noqa: F401
+    iters_per_solve = int(os.environ.get("GPE_BENCH_ITERS_PER_SOLVE", "0")) or 3000
+    for _ in range(args.warmup):
+        oracle_sample(seconds=1.0, max_iters=20)
+    times = []
+    for _ in range(args.steps):
+        t_it, k = oracle_sample(seconds=8.0, max_iters=200)
+        times.append(t_it * iters_per_solve)
+    ms = 1000.0 * statistics.mean(times)
+    val = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "256x256", "eta": 1000.0, "omega": 0.9,
+                       "tol_res_inf": 1e-8, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: up to 200 FP64 numpy PCG_C iterations of {WORKLOAD} "
+                                       f"(~8 s), time/iteration x {iters_per_solve} iterations per solve"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1611_02045_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1611_02045_gb300 import gpe, inputs as I
+
+    stream = torch.cuda.current_stream()
+    w = I.workload(WORKLOAD)
+    n, L = w["n"], w["L"]
+    N = int(np.prod(n))
+    ctx = gpe.Context(n, L, w["eta"], w["omega"], w["V"], prec=gpe.GPE_MIXED)
+    phi0_d = torch.from_numpy(w["phi0"].copy()).to(dev)
+    phi_d = torch.empty_like(phi0_d)
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def solve_dev():
+        phi_d.copy_(phi0_d)
+        return ctx.pcg_solve(phi_d, check=True)
+
+    for _ in range(max(args.warmup, 3)):
+        rep = solve_dev()
+    iters_total, iters_lo = rep["iters"], rep["iters_lo"]
+
+    # ---------------- timed region: K solves, L2 flushed before each ----------------
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    step_ms, reps = [], []
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        reps.append(solve_dev())
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    launches = 0
+    for r in reps:
+        it, lo = r["iters"], r["iters_lo"]
+        launches += 2 + (1 + 7 * (lo + 1)) + (1 + 7 * (it - lo + 1))
+
+    # ---------------- e2e: phi in pinned host memory ----------------
+    phi_h0 = torch.from_numpy(w["phi0"].copy()).pin_memory()
+    phi_h = torch.empty_like(phi_h0).pin_memory()
+    e2e_ms = []
+    for _ in range(args.steps):
+        phi_h.copy_(phi_h0)
+        l2_flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pcg_solve(phi_h.data_ptr(), check=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+
+    # ---------------- roofline: H phi on a grid larger than L2 ----------------
+    hn = HPHI_GRID
+    HN = int(np.prod(hn))
+    hL = (8.0, 8.0, 8.0)
+    Vh = torch.zeros(HN, dtype=torch.float64, device=dev)
+    hctx = gpe.Context(hn, hL, 100.0, 0.5, Vh, prec=gpe.GPE_MIXED)
+    del Vh
+    g = torch.Generator(device=dev).manual_seed(1)
+    hphi = torch.randn(HN, dtype=torch.complex64, device=dev, generator=g)
+    hout = torch.empty_like(hphi)
+    for _ in range(3):
+        hctx.apply_H(hphi, hphi, hout)
+    torch.cuda.synchronize()
+    hms = []
+    for _ in range(20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hctx.apply_H(hphi, hphi, hout)
+        b.record(stream)
+        b.synchronize()
+        hms.append(a.elapsed_time(b))
+    h_ms = statistics.median(hms)
+    achieved = HPHI_BYTES_PER_PT * HN / (h_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    hctx.close()
+    del hphi, hout
+
+    # ---------------- secondary: the 128^3 workload ----------------
+    secondary = None
+    if not args.no_secondary:
+        w3 = I.workload("rot128_3d")
+        ctx3 = gpe.Context(w3["n"], w3["L"], w3["eta"], w3["omega"], w3["V"], prec=gpe.GPE_MIXED)
+        p30 = torch.from_numpy(w3["phi0"].copy()).to(dev)
+        p3 = torch.empty_like(p30)
+        p3.copy_(p30)
+        r3 = ctx3.pcg_solve(p3, check=True)  # warm-up (graph build)
+        s3 = []
+        for _ in range(2):
+            p3.copy_(p30)
+            l2_flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r3 = ctx3.pcg_solve(p3, check=True)
+            b.record(stream)
+            b.synchronize()
+            s3.append(a.elapsed_time(b))
+        secondary = {"workload": "rot128_3d", "value": 1000.0 / statistics.mean(s3), "unit": UNIT,
+                     "ms_per_step": statistics.mean(s3), "iters": r3["iters"], "iters_lo": r3["iters_lo"],
+                     "E": r3["E"], "res_inf": r3["res_inf"]}
+        ctx3.close()
+
+    # ---------------- CPU baseline (oracle, bounded sample) ----------------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_it, k = oracle_sample(seconds=12.0)
+        cpu = {"value": 1.0 / (t_it * iters_total), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} FP64 numpy PCG_C iterations of {WORKLOAD} ({t_it*1e3:.1f} ms/iteration, "
+                         f"1 thread), scaled by the {iters_total} iterations of the GPU solve"}
+
+    if rank == 0:
+        last = reps[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "256x256", "domain": "[-16,16]^2", "eta": 1000.0,
+                       "omega": 0.9, "V": "r^2/2", "precision": "mixed (c64 phase, c128 refinement)",
+                       "tol_res_inf": 1e-8, "iters": last["iters"], "iters_c64": last["iters_lo"],
+                       "E": last["E"], "res_inf": last["res_inf"],
+                       "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "H phi = pass_x<HX> + pass_s<HMID> (y, z) of gpe_apply_H, complex64",
+                         "grid": "x".join(map(str, hn)), "bytes_per_launch": HPHI_BYTES_PER_PT * HN,
+                         "ms_per_launch": h_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "secondary": secondary,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

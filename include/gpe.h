@@ -1,0 +1,172 @@
+/*
+ * gpe.h -- C ABI of libgpe: the hot path of the preconditioned nonlinear
+ * conjugate gradient method (PCG_C) of Antoine, Levitt and Tang,
+ * "Efficient spectral computation of the stationary states of rotating
+ * Bose-Einstein condensates by the preconditioned nonlinear conjugate
+ * gradient method" (arXiv:1611.02045), on one GB300 GPU.
+ *
+ * Problem (paper Section 2): minimise, over ||phi|| = 1,
+ *   E(phi) = int 1/2|grad phi|^2 + V|phi|^2 + eta/2 |phi|^4 - omega conj(phi) L_z phi,
+ *   L_z = -i (x d_y - y d_x),
+ * discretised on the periodic grid of Section 3: x_k = -L + k h, h = 2L/M,
+ * Fourier frequencies xi_p = p pi / L for p = -M/2 .. M/2-1, derivatives by
+ * per-axis DFTs (eq. FFTdiscret).
+ *
+ * Conventions shared by every entry point
+ *  - Fields are complex arrays stored [z][y][x], x fastest, interleaved
+ *    (re, im).  Their element type is the context's working precision:
+ *    complex128 for GPE_FP64, complex64 for GPE_MIXED (the exception is
+ *    gpe_pcg_solve, whose phi is always complex128).
+ *  - Inner products carry the quadrature weight h^d:
+ *    <f, g> = h_x h_y [h_z] sum conj(f_k) g_k, so ||phi||^2 = h^d sum |phi_k|^2.
+ *  - Pointers named *_dev must be device memory of the current device;
+ *    pointers documented "host or device" are classified with
+ *    cudaPointerGetAttributes and copied as needed.
+ *  - All work is ordered on the stream given to gpe_create.  Calls that
+ *    return host scalars (gpe_energy, gpe_pcg_solve) synchronise it.
+ *  - No exception crosses the ABI: every call returns a gpe_status and, on
+ *    failure, gpe_last_error() describes the cause.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPE_OK = 0,
+  GPE_ERR_ARG = 1,           /* invalid argument (sizes, null pointers, L <= 0, ...) */
+  GPE_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  GPE_ERR_NOT_CONVERGED = 3, /* max_iter reached before the stopping rule held */
+  GPE_ERR_NONFINITE = 4,     /* NaN/Inf met in a reduction */
+  GPE_ERR_PRECOND = 5,       /* alpha + V + eta|phi|^2 <= 0 somewhere (P_V undefined) */
+  GPE_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  GPE_ERR_UNSUPPORTED = 7    /* configuration not supported by this build */
+} gpe_status;
+
+typedef enum {
+  GPE_FP64 = 0,  /* complex128 fields, FP64 everywhere */
+  GPE_MIXED = 1  /* complex64 transforms and pointwise work, FP64 reductions,
+                    then a complex128 refinement phase */
+} gpe_precision;
+
+/* Discrete problem (Sections 2-3).  n[i]: points on axis i (x, y, z), each a
+ * power of two in [8, 512]; L[i] > 0: the domain is [-L_i, L_i).  dim = 2
+ * ignores n[2], L[2].  Rotation is about the z axis. */
+typedef struct {
+  int dim;
+  int n[3];
+  double L[3];
+  double eta;    /* nonlinearity (the paper's eta) */
+  double omega;  /* rotation speed (the paper's omega) */
+  gpe_precision prec;
+} gpe_problem;
+
+/* Solver options.  gpe_solve_opts_default fills the values in brackets. */
+typedef struct {
+  double tol_res_inf;   /* stop when ||H phi_n - lambda_n phi_n||_inf < tol (eq. Stop_Residual) [1e-8] */
+  double tol_dE;        /* > 0: also stop when |E_{n+1} - E_n| <= tol_dE (eq. Stop_Energy) [0] */
+  int max_iter;         /* total iteration cap over both phases [20000] */
+  double theta_default; /* trial step when the model curvature is <= 0 (Section 5.1) [0.1] */
+  int max_backtracks;   /* trial step halvings before a step is taken anyway [30] */
+  int cg;               /* 1: Algorithm 2 (PCG), 0: Algorithm 1 (PG) [1] */
+  /* GPE_MIXED only: the complex64 phase ends, and the complex128 phase
+   * restarts the conjugate directions, when ||r||_inf has not halved within
+   * stall_window iterations, or falls below switch_res. */
+  int stall_window;     /* [40] */
+  double switch_res;    /* [1e-6] */
+  int max_iter_lo;      /* cap on complex64-phase iterations [max_iter] */
+  int use_graph;        /* 1: one CUDA graph launch with a device-side loop; 0: host loop [1] */
+} gpe_solve_opts;
+
+/* Per-iteration log row, doubles: */
+#define GPE_LOG_FIELDS 12
+/* n, phase (0 = complex64, 1 = complex128), E_n, lambda_n, ||r_n||_inf,
+ * ||r_n||_2, alpha_n (shift of P_C), beta_n (after max(.,0) and the
+ * descent check), theta_n, Delta E_n (accepted step), fallback (1 = gradient
+ * step taken), backtracks */
+
+typedef struct {
+  int status;        /* gpe_status of the solve */
+  int iters;         /* iterations n performed (phi returned is phi_n) */
+  int iters_lo;      /* of which in the complex64 phase */
+  int fallbacks;     /* gradient-step fallbacks (Section 5.2) */
+  int backtracks;    /* total step halvings */
+  double E;          /* E(phi_n) */
+  double lambda;     /* lambda_n = <phi_n, H phi_n> */
+  double res_inf;    /* ||r_n||_inf */
+  double res_l2;     /* ||r_n||_2 (weighted) */
+  int log_cap;       /* in: rows available in log (0: no log) */
+  int log_len;       /* out: rows written (min(iters + 1, log_cap)) */
+  double* log;       /* in: host array [log_cap][GPE_LOG_FIELDS] or NULL */
+} gpe_report;
+
+typedef struct gpe_ctx gpe_ctx;
+
+/* Fill *opts with the defaults above.  Returns GPE_ERR_ARG if opts is NULL. */
+gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
+
+/* Create a context for problem *prob.
+ *  V      : real potential on the grid, float64, [z][y][x]; host or device;
+ *           copied (the caller keeps ownership).
+ *  stream : cudaStream_t (NULL = legacy default stream) that orders all work.
+ * Allocates all device workspace (fields, tables, reduction buffers) once.
+ * Errors: GPE_ERR_ARG (null pointers, dim not 2/3, n not a power of two in
+ * [8,512], L <= 0, non-finite eta/omega), GPE_ERR_CUDA. */
+gpe_status gpe_create(const gpe_problem* prob, const double* V, void* stream, gpe_ctx** out);
+
+/* Release everything the context owns.  NULL is accepted. */
+gpe_status gpe_destroy(gpe_ctx* ctx);
+
+/* out = H_phi f = -1/2 Delta f + V f + eta |phi|^2 f - omega L_z f
+ * (Section 2; discrete operators of eq. FFTdiscret).  phi_dev, f_dev,
+ * out_dev: device fields in working precision; out may alias f but not phi.
+ * Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
+gpe_status gpe_apply_H(gpe_ctx* ctx, const void* phi_dev, const void* f_dev, void* out_dev);
+
+/* out = P_C r = P_V^{1/2} P_Delta P_V^{1/2} r (eq. combinedP_12) with
+ * P_Delta = (alpha - Delta/2)^{-1} (eq. PDelta) and
+ * P_V = (alpha + V + eta |phi|^2)^{-1} (eq. PV).  alpha <= 0 selects the
+ * paper's adaptive shift lambda~(phi) = int 1/2|grad phi|^2 + V|phi|^2 +
+ * eta|phi|^4 (eq. Opt_Alpha), computed on the device.  Fields as for
+ * gpe_apply_H; out may alias r.  Asynchronous.  Errors: GPE_ERR_ARG,
+ * GPE_ERR_CUDA. */
+gpe_status gpe_precond(gpe_ctx* ctx, const void* phi_dev, const void* r_dev, double alpha, void* out_dev);
+
+/* Energy terms of phi (Section 2), host doubles:
+ * out[0] kinetic int 1/2|grad phi|^2, out[1] potential int V|phi|^2,
+ * out[2] interaction eta/2 int |phi|^4, out[3] rotation -omega <phi, L_z phi>,
+ * out[4] total E, out[5] lambda = <phi, H_phi phi>, out[6] lambda~ (eq. Opt_Alpha),
+ * out[7] ||phi||^2.  phi is not normalised first.  Synchronises the stream.
+ * Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
+gpe_status gpe_energy(gpe_ctx* ctx, const void* phi_dev, double out[8]);
+
+/* Ground state by Algorithm 2 (PCG) with the symmetric combined
+ * preconditioner P_C, the Polak-Ribiere coefficient beta = max(beta_PR, 0)
+ * (eq. CG:PR), the descent check of Section 5.2, the step-size heuristic and
+ * energy-decrease backtracking of Section 5.1, and renormalisation after
+ * every step.
+ *  phi_inout : complex128 [z][y][x], host or device.  In: initial guess (need
+ *              not be normalised).  Out: the last iterate phi_n.
+ *  opts      : NULL = defaults.
+ *  report    : may be NULL.
+ * GPE_MIXED runs a complex64 phase, then a complex128 phase from its result.
+ * Synchronises the stream.  Returns GPE_OK when the stopping rule held, else
+ * GPE_ERR_NOT_CONVERGED / GPE_ERR_NONFINITE / GPE_ERR_PRECOND / GPE_ERR_ARG /
+ * GPE_ERR_CUDA (report->status carries the same code). */
+gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* opts, gpe_report* report);
+
+/* Human-readable description of the last failure on ctx ("" if none).
+ * The string is owned by ctx and valid until its next call. ctx NULL gives
+ * the message of the last failed gpe_create. */
+const char* gpe_last_error(const gpe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPE_H */

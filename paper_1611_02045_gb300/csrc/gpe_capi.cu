@@ -1,0 +1,530 @@
+// gpe_capi.cu -- the C ABI of include/gpe.h: context set-up (grid tables,
+// workspace), pass planning, the operator entry points and the PCG_C solve
+// (Algorithm 2 of arXiv:1611.02045) as one CUDA graph with a device-side
+// WHILE loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gpe.h"
+#include "gpe_internal.h"
+
+using namespace gpe;
+
+namespace {
+
+constexpr int kTargetBlocks = 2 * 152;  // aim for >= 2 blocks per SM per pass
+
+struct PassPlan {
+  int lpb = 1, tx = 1, nblocks = 1, M = 8;
+  long long stride = 0, outer_stride = 0;
+  int ntx = 1;
+};
+
+struct PrecBufs {
+  bool on = false;
+  void* xi[3] = {nullptr, nullptr, nullptr};
+  void* xc[3] = {nullptr, nullptr, nullptr};
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* V = nullptr;
+  void* phi = nullptr;
+  void* p = nullptr;
+  void* t = nullptr;
+  void* s = nullptr;
+  void* r_prev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct gpe_ctx {
+  gpe_problem prob{};
+  int dim = 2, n[3] = {1, 1, 1};
+  long long N = 0;
+  double h[3] = {1, 1, 1}, weight = 1.0;
+  cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  std::string err;
+  PrecBufs pb[2];  // 0: float / complex64, 1: double / complex128
+  int work = 1;    // precision of API calls
+  Ctl* ctl_solve = nullptr;
+  Ctl* ctl_api = nullptr;
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  double* log_dev = nullptr;
+  int log_dev_cap = 0;
+  PassPlan plan[3];  // per axis
+  int max_threads[2] = {512, 256};
+  bool warmed[2] = {false, false};
+};
+
+#define GPE_CU(ctx, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return GPE_ERR_CUDA;                                                                 \
+    }                                                                                      \
+  } while (0)
+
+static bool is_pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void plan_axis(gpe_ctx* c, int axis, int maxT, PassPlan& pl) {
+  const int M = c->n[axis];
+  const int Tl = M / 8;
+  pl.M = M;
+  if (axis == 0) {
+    const long long nlines = (long long)c->n[1] * (c->dim == 3 ? c->n[2] : 1);
+    int lpb = maxT / Tl;
+    if (lpb < 1) lpb = 1;
+    while (lpb > 1 && (lpb > nlines || nlines / lpb < kTargetBlocks)) lpb >>= 1;
+    pl.lpb = lpb;
+    pl.nblocks = (int)(nlines / lpb);
+  } else {
+    const int nx = c->n[0];
+    const long long outer = (axis == 1) ? (c->dim == 3 ? c->n[2] : 1) : c->n[1];
+    int tx = 16;
+    if (tx > nx) tx = nx;
+    while (tx > 1 && tx * Tl > maxT) tx >>= 1;
+    while (tx > 4 && (long long)(nx / tx) * outer < kTargetBlocks) tx >>= 1;
+    pl.tx = tx;
+    pl.ntx = nx / tx;
+    pl.nblocks = (int)((long long)pl.ntx * outer);
+    pl.stride = (axis == 1) ? nx : (long long)nx * c->n[1];
+    pl.outer_stride = (axis == 1) ? (long long)nx * c->n[1] : nx;
+  }
+}
+
+static PassArgs base_args(gpe_ctx* c, int prec, int axis) {
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const PassPlan& pl = c->plan[axis];
+  const PrecBufs& b = c->pb[prec];
+  a.dim = c->dim; a.nx = c->n[0]; a.ny = c->n[1]; a.nz = c->dim == 3 ? c->n[2] : 1;
+  a.axis = axis; a.M = pl.M; a.lpb = pl.lpb; a.tx = pl.tx; a.stride = pl.stride;
+  a.outer_stride = pl.outer_stride; a.ntx = pl.ntx; a.nblocks = pl.nblocks;
+  a.weight = c->weight; a.eta = c->prob.eta; a.omega = c->prob.omega;
+  for (int i = 0; i < 3; ++i) { a.xi[i] = b.xi[i]; a.xc[i] = b.xc[i]; }
+  a.tw = b.tw[axis];
+  a.V = b.V;
+  a.partials = c->partials;
+  a.ticket = c->ticket;
+  return a;
+}
+
+static cudaError_t launch(int prec, Pass pass, const PassArgs& a, cudaStream_t st) {
+  return prec ? launch_pass_f64(pass, a, st) : launch_pass_f32(pass, a, st);
+}
+
+template <typename T>
+static cudaError_t upload_tables(gpe_ctx* c, PrecBufs& b) {
+  for (int i = 0; i < c->dim; ++i) {
+    const int M = c->n[i];
+    const double L = c->prob.L[i];
+    std::vector<T> xi(M), xc(M), tw(2 * M);
+    for (int p = 0; p < M; ++p) {
+      const int pp = p < M / 2 ? p : p - M;  // xi_p = p pi / L, p = -M/2 .. M/2-1
+      xi[p] = (T)(pp * M_PI / L);
+      xc[p] = (T)(-L + p * (2.0 * L / M));   // x_k = -L + k h
+      tw[2 * p] = (T)std::cos(2.0 * M_PI * p / M);
+      tw[2 * p + 1] = (T)(-std::sin(2.0 * M_PI * p / M));
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&b.xi[i], M * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&b.xc[i], M * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&b.tw[i], 2 * M * sizeof(T))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b.xi[i], xi.data(), M * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b.xc[i], xc.data(), M * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(b.tw[i], tw.data(), 2 * M * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
+  PrecBufs& b = c->pb[prec];
+  b.on = true;
+  const size_t cb = prec ? 16 : 8;
+  const size_t bytes = cb * (size_t)c->N;
+  GPE_CU(c, prec ? upload_tables<double>(c, b) : upload_tables<float>(c, b));
+  GPE_CU(c, cudaMalloc(&b.phi, bytes));
+  GPE_CU(c, cudaMalloc(&b.p, bytes));
+  GPE_CU(c, cudaMalloc(&b.t, bytes));
+  GPE_CU(c, cudaMalloc(&b.s, bytes));
+  GPE_CU(c, cudaMalloc(&b.r_prev, bytes));
+  GPE_CU(c, cudaMemset(b.p, 0, bytes));
+  GPE_CU(c, cudaMemset(b.r_prev, 0, bytes));
+  if (prec) {
+    GPE_CU(c, cudaMalloc(&b.V, 8 * (size_t)c->N));
+    GPE_CU(c, cudaMemcpy(b.V, Vdev64, 8 * (size_t)c->N, cudaMemcpyDeviceToDevice));
+  } else {
+    GPE_CU(c, cudaMalloc(&b.V, 4 * (size_t)c->N));
+    GPE_CU(c, launch_d2f(Vdev64, (float*)b.V, c->N, 0));
+    GPE_CU(c, cudaDeviceSynchronize());
+  }
+  return GPE_OK;
+}
+
+static void free_ctx(gpe_ctx* c) {
+  for (auto& b : c->pb) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    for (int i = 0; i < 3; ++i) { cudaFree(b.xi[i]); cudaFree(b.xc[i]); cudaFree(b.tw[i]); }
+    cudaFree(b.V); cudaFree(b.phi); cudaFree(b.p); cudaFree(b.t); cudaFree(b.s); cudaFree(b.r_prev);
+  }
+  cudaFree(c->ctl_solve); cudaFree(c->ctl_api); cudaFree(c->partials); cudaFree(c->ticket); cudaFree(c->log_dev);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
+  if (!o) return GPE_ERR_ARG;
+  o->tol_res_inf = 1e-8;
+  o->tol_dE = 0.0;
+  o->max_iter = 20000;
+  o->theta_default = 0.1;
+  o->max_backtracks = 30;
+  o->cg = 1;
+  o->stall_window = 40;
+  o->switch_res = 1e-6;
+  o->max_iter_lo = 0;
+  o->use_graph = 1;
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void* stream, gpe_ctx** out) {
+  if (!prob || !V || !out) { g_create_error = "null argument"; return GPE_ERR_ARG; }
+  *out = nullptr;
+  if (prob->dim != 2 && prob->dim != 3) { g_create_error = "dim must be 2 or 3"; return GPE_ERR_ARG; }
+  for (int i = 0; i < prob->dim; ++i) {
+    if (!is_pow2_in(prob->n[i], 8, 512)) { g_create_error = "n[i] must be a power of two in [8, 512]"; return GPE_ERR_ARG; }
+    if (!(prob->L[i] > 0.0) || !std::isfinite(prob->L[i])) { g_create_error = "L[i] must be finite and > 0"; return GPE_ERR_ARG; }
+  }
+  if (!std::isfinite(prob->eta) || !std::isfinite(prob->omega)) { g_create_error = "eta/omega must be finite"; return GPE_ERR_ARG; }
+  if (prob->prec != GPE_FP64 && prob->prec != GPE_MIXED) { g_create_error = "unknown precision"; return GPE_ERR_ARG; }
+
+  gpe_ctx* c = new gpe_ctx();
+  c->prob = *prob;
+  c->dim = prob->dim;
+  c->N = 1;
+  c->weight = 1.0;
+  for (int i = 0; i < c->dim; ++i) {
+    c->n[i] = prob->n[i];
+    c->h[i] = 2.0 * prob->L[i] / prob->n[i];
+    c->N *= prob->n[i];
+    c->weight *= c->h[i];
+  }
+  c->st = (cudaStream_t)stream;
+  c->work = prob->prec == GPE_FP64 ? 1 : 0;
+  auto fail = [&](gpe_status s) { g_create_error = c->err; free_ctx(c); return s; };
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) { c->err = "stream create failed"; return fail(GPE_ERR_CUDA); }
+
+  // potential: keep a device float64 copy as the source of both precisions
+  double* V64 = nullptr;
+  if (cudaMalloc(&V64, 8 * (size_t)c->N) != cudaSuccess) { c->err = "cudaMalloc V"; return fail(GPE_ERR_CUDA); }
+  if (cudaMemcpy(V64, V, 8 * (size_t)c->N, cudaMemcpyDefault) != cudaSuccess) {
+    cudaFree(V64); c->err = "copy of V failed"; return fail(GPE_ERR_CUDA);
+  }
+  gpe_status s = alloc_prec(c, 1, V64);
+  if (s == GPE_OK && prob->prec == GPE_MIXED) s = alloc_prec(c, 0, V64);
+  cudaFree(V64);
+  if (s != GPE_OK) return fail(s);
+
+  int maxblocks = 1;
+  for (int ax = 0; ax < c->dim; ++ax) {
+    // plan with the smaller (double) thread cap so one plan serves both precisions
+    plan_axis(c, ax, c->max_threads[1], c->plan[ax]);
+    if (c->plan[ax].nblocks > maxblocks) maxblocks = c->plan[ax].nblocks;
+  }
+  if (cudaMalloc(&c->ctl_solve, sizeof(Ctl)) != cudaSuccess || cudaMalloc(&c->ctl_api, sizeof(Ctl)) != cudaSuccess ||
+      cudaMalloc(&c->partials, sizeof(double) * kMaxMoments * (size_t)maxblocks) != cudaSuccess ||
+      cudaMalloc(&c->ticket, sizeof(unsigned)) != cudaSuccess) {
+    c->err = "cudaMalloc workspace"; return fail(GPE_ERR_CUDA);
+  }
+  cudaMemset(c->ctl_solve, 0, sizeof(Ctl));
+  cudaMemset(c->ctl_api, 0, sizeof(Ctl));
+  cudaMemset(c->ticket, 0, sizeof(unsigned));
+  if (cudaDeviceSynchronize() != cudaSuccess) { c->err = "set-up failed"; return fail(GPE_ERR_CUDA); }
+  *out = c;
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_destroy(gpe_ctx* c) {
+  if (!c) return GPE_OK;
+  cudaStreamSynchronize(c->st);
+  free_ctx(c);
+  return GPE_OK;
+}
+
+extern "C" const char* gpe_last_error(const gpe_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+// H passes on (phi, f): t = A_x f + (V + eta|phi|^2) f, then the y (and z) parts
+// accumulated; the last one writes `out` (or t) and finalises the energy terms.
+static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, void* out, Ctl* ctl) {
+  PassArgs a = base_args(c, prec, 0);
+  a.ctl = ctl; a.phi = phi; a.f = f; a.t = c->pb[prec].t;
+  GPE_CU(c, launch(prec, P_HX, a, c->st));
+  for (int ax = 1; ax < c->dim; ++ax) {
+    PassArgs b = base_args(c, prec, ax);
+    b.ctl = ctl; b.phi = phi; b.f = f; b.t = c->pb[prec].t;
+    b.last_axis = (ax == c->dim - 1);
+    b.out = b.last_axis ? out : nullptr;
+    GPE_CU(c, launch(prec, P_HMID, b, c->st));
+  }
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_apply_H(gpe_ctx* c, const void* phi, const void* f, void* out) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !f || !out) { c->err = "null field pointer"; return GPE_ERR_ARG; }
+  return run_H(c, c->work, phi, f, out, c->ctl_api);
+}
+
+extern "C" gpe_status gpe_energy(gpe_ctx* c, const void* phi, double out[8]) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !out) { c->err = "null pointer"; return GPE_ERR_ARG; }
+  const int prec = c->work;
+  gpe_status s = run_H(c, prec, phi, phi, c->pb[prec].t, c->ctl_api);
+  if (s != GPE_OK) return s;
+  Ctl h;
+  GPE_CU(c, cudaMemcpyAsync(&h, c->ctl_api, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  out[0] = h.kin; out[1] = h.pot; out[2] = 0.5 * c->prob.eta * h.U0; out[3] = h.rot;
+  out[4] = h.E; out[5] = h.lam; out[6] = h.alpha; out[7] = h.norm2;
+  return GPE_OK;
+}
+
+// P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
+static gpe_status run_PC(gpe_ctx* c, int prec, const void* phi, const void* r, double alpha, void* out, Ctl* ctl,
+                         bool solver) {
+  PassArgs a = base_args(c, prec, 0);
+  a.ctl = ctl; a.solver = solver; a.phi = phi; a.r_in = r; a.api_alpha = alpha;
+  a.s = c->pb[prec].s; a.t = c->pb[prec].t; a.r_prev = c->pb[prec].r_prev; a.p = c->pb[prec].p; a.out = out;
+  GPE_CU(c, launch(prec, P_C1, a, c->st));
+  if (c->dim == 3) {
+    PassArgs b = base_args(c, prec, 1);
+    b.ctl = ctl; b.solver = solver; b.s = a.s;
+    GPE_CU(c, launch(prec, P_CFWD, b, c->st));
+  }
+  PassArgs k = base_args(c, prec, c->dim - 1);
+  k.ctl = ctl; k.solver = solver; k.s = a.s; k.api_alpha = alpha;
+  GPE_CU(c, launch(prec, P_CCORE, k, c->st));
+  if (c->dim == 3) {
+    PassArgs b = base_args(c, prec, 1);
+    b.ctl = ctl; b.solver = solver; b.s = a.s;
+    GPE_CU(c, launch(prec, P_CINV, b, c->st));
+  }
+  GPE_CU(c, launch(prec, P_C3, a, c->st));
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_precond(gpe_ctx* c, const void* phi, const void* r, double alpha, void* out) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !r || !out) { c->err = "null field pointer"; return GPE_ERR_ARG; }
+  if (!std::isfinite(alpha)) { c->err = "alpha must be finite"; return GPE_ERR_ARG; }
+  const int prec = c->work;
+  if (!(alpha > 0.0)) {
+    gpe_status s = run_H(c, prec, phi, phi, c->pb[prec].t, c->ctl_api);  // lambda~ into ctl_api->alpha
+    if (s != GPE_OK) return s;
+  }
+  return run_PC(c, prec, phi, r, alpha, out, c->ctl_api, false);
+}
+
+// One PCG iteration (all passes) in precision prec, on the solver buffers.
+static gpe_status enqueue_iteration(gpe_ctx* c, int prec, cudaStream_t st, unsigned long long cond) {
+  PrecBufs& b = c->pb[prec];
+  Ctl* ctl = c->ctl_solve;
+  cudaStream_t keep = c->st;
+  c->st = st;
+  gpe_status s = GPE_OK;
+  do {
+    // H phi (with the retraction phi_{n+1} = (c phi_n + s p_n/|p_n|)/nrm folded into the x pass)
+    PassArgs a = base_args(c, prec, 0);
+    a.ctl = ctl; a.solver = 1; a.phi = b.phi; a.phi_out = b.phi; a.p = b.p; a.t = b.t;
+    if (launch(prec, P_HX, a, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
+    for (int ax = 1; ax < c->dim && s == GPE_OK; ++ax) {
+      PassArgs h = base_args(c, prec, ax);
+      h.ctl = ctl; h.solver = 1; h.phi = b.phi; h.t = b.t; h.last_axis = (ax == c->dim - 1);
+      if (launch(prec, P_HMID, h, st) != cudaSuccess) s = GPE_ERR_CUDA;
+    }
+    if (s != GPE_OK) break;
+    // P_C r_n
+    s = run_PC(c, prec, b.phi, nullptr, 0.0, nullptr, ctl, true);
+    if (s != GPE_OK) break;
+    // p_n and the step-size moments
+    PassArgs x = base_args(c, prec, 0);
+    x.ctl = ctl; x.solver = 1; x.phi = b.phi; x.s = b.s; x.t = b.t; x.p = b.p;
+    if (launch(prec, P_AX, x, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
+    for (int ax = 1; ax < c->dim; ++ax) {
+      PassArgs m = base_args(c, prec, ax);
+      m.ctl = ctl; m.solver = 1; m.phi = b.phi; m.p = b.p; m.last_axis = (ax == c->dim - 1);
+      m.cond = m.last_axis ? cond : 0ull;
+      if (launch(prec, P_AMID, m, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
+    }
+  } while (0);
+  c->st = keep;
+  if (s != GPE_OK) c->err = std::string("pass launch failed: ") + cudaGetErrorString(cudaGetLastError());
+  return s;
+}
+
+static gpe_status build_graph(gpe_ctx* c, int prec) {
+  PrecBufs& b = c->pb[prec];
+  if (b.exec) return GPE_OK;
+  cudaGraph_t g = nullptr;
+  GPE_CU(c, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  GPE_CU(c, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  GPE_CU(c, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  GPE_CU(c, cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  gpe_status s = enqueue_iteration(c, prec, c->cap, (unsigned long long)h);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &captured);
+  if (s != GPE_OK) { cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) { c->err = std::string("capture: ") + cudaGetErrorString(e); cudaGraphDestroy(g); return GPE_ERR_CUDA; }
+  e = cudaGraphInstantiate(&b.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { c->err = std::string("instantiate: ") + cudaGetErrorString(e); b.exec = nullptr; return GPE_ERR_CUDA; }
+  return GPE_OK;
+}
+
+// Make sure every pass kernel of precision prec has had its attributes set
+// (first launch) before capture: one iteration with done = 1 exits at once.
+static gpe_status warm_kernels(gpe_ctx* c, int prec) {
+  if (c->warmed[prec]) return GPE_OK;
+  Ctl h;
+  std::memset(&h, 0, sizeof(h));
+  h.done = 1;
+  GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+  gpe_status s = enqueue_iteration(c, prec, c->st, 0ull);
+  if (s != GPE_OK) return s;
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  c->warmed[prec] = true;
+  return GPE_OK;
+}
+
+static gpe_status run_phase(gpe_ctx* c, int prec, Ctl& h, const gpe_solve_opts& o) {
+  PrecBufs& b = c->pb[prec];
+  const size_t bytes = (prec ? 16 : 8) * (size_t)c->N;
+  gpe_status s = warm_kernels(c, prec);
+  if (s != GPE_OK) return s;
+  GPE_CU(c, cudaMemsetAsync(b.p, 0, bytes, c->st));
+  GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, bytes, c->st));
+  GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+  GPE_CU(c, launch_init_norm(prec, b.phi, c->N, c->weight, c->ctl_solve, c->st));
+  if (o.use_graph) {
+    s = build_graph(c, prec);
+    if (s != GPE_OK) return s;
+    GPE_CU(c, cudaGraphLaunch(b.exec, c->st));
+  } else {
+    int k = 0;
+    while (true) {
+      s = enqueue_iteration(c, prec, c->st, 0ull);
+      if (s != GPE_OK) return s;
+      if (++k % 16 == 0) {
+        int done = 0;
+        GPE_CU(c, cudaMemcpyAsync(&done, &c->ctl_solve->done, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        GPE_CU(c, cudaStreamSynchronize(c->st));
+        if (done) break;
+      }
+    }
+  }
+  GPE_CU(c, cudaMemcpyAsync(&h, c->ctl_solve, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve_opts* opts, gpe_report* rep) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi_inout) { c->err = "null phi"; return GPE_ERR_ARG; }
+  gpe_solve_opts o;
+  gpe_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1) {
+    c->err = "invalid solve options";
+    return GPE_ERR_ARG;
+  }
+  if (o.max_iter_lo <= 0) o.max_iter_lo = o.max_iter;
+  const int log_cap = (rep && rep->log && rep->log_cap > 0) ? rep->log_cap : 0;
+  if (log_cap > c->log_dev_cap) {
+    cudaFree(c->log_dev);
+    c->log_dev = nullptr;
+    c->log_dev_cap = 0;
+    GPE_CU(c, cudaMalloc(&c->log_dev, sizeof(double) * kLogFields * (size_t)log_cap));
+    c->log_dev_cap = log_cap;
+  }
+  const bool dev = is_device_ptr(phi_inout);
+  const size_t b128 = 16 * (size_t)c->N;
+  GPE_CU(c, cudaMemcpyAsync(c->pb[1].phi, phi_inout, b128, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+
+  Ctl h;
+  std::memset(&h, 0, sizeof(h));
+  h.tol_res_inf = o.tol_res_inf; h.tol_dE = o.tol_dE; h.theta_default = o.theta_default; h.switch_res = o.switch_res;
+  h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
+  h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
+  h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
+
+  int iters_lo = 0;
+  gpe_status s;
+  if (c->prob.prec == GPE_MIXED) {
+    GPE_CU(c, launch_convert_c128_to_c64(c->pb[1].phi, c->pb[0].phi, c->N, c->st));
+    h.lo_phase = 1; h.phase = 0; h.iter_phase0 = 0; h.max_iter_phase = o.max_iter_lo;
+    s = run_phase(c, 0, h, o);
+    if (s != GPE_OK) return s;
+    iters_lo = h.iter;
+    const bool go_on = h.switch_req || h.status == 0;  // a complex64 "success" is refined too
+    if (h.status == GPE_ERR_NONFINITE || h.status == GPE_ERR_PRECOND) {
+      // keep the input in the complex128 buffer; report the failure
+    } else if (go_on) {
+      GPE_CU(c, launch_convert_c64_to_c128(c->pb[0].phi, c->pb[1].phi, c->N, c->st));
+    }
+    if (go_on && h.iter < o.max_iter) {
+      h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = 1; h.stop_dE = 0;
+      h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter;
+      s = run_phase(c, 1, h, o);
+      if (s != GPE_OK) return s;
+    }
+  } else {
+    h.lo_phase = 0; h.phase = 1; h.max_iter_phase = o.max_iter;
+    s = run_phase(c, 1, h, o);
+    if (s != GPE_OK) return s;
+  }
+  GPE_CU(c, cudaMemcpyAsync(phi_inout, c->pb[1].phi, b128, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  if (rep) {
+    rep->status = h.status; rep->iters = h.iter; rep->iters_lo = iters_lo;
+    rep->fallbacks = h.fallbacks; rep->backtracks = h.backtracks_total;
+    rep->E = h.E; rep->lambda = h.lam; rep->res_inf = h.res_inf; rep->res_l2 = h.res_l2;
+    rep->log_len = 0;
+    if (log_cap) {
+      int nrows = h.iter + 1 < log_cap ? h.iter + 1 : log_cap;
+      GPE_CU(c, cudaMemcpy(rep->log, c->log_dev, sizeof(double) * kLogFields * (size_t)nrows, cudaMemcpyDeviceToHost));
+      rep->log_len = nrows;
+    }
+  }
+  if (h.status != GPE_OK) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "solve ended with status %d after %d iterations (res_inf %.3e)", h.status, h.iter,
+                  h.res_inf);
+    c->err = buf;
+  }
+  return (gpe_status)h.status;
+}

@@ -1,0 +1,159 @@
+// gpe_fft.cuh -- in-register / shared-memory line DFTs for the per-axis
+// spectral operators of eq. FFTdiscret (arXiv:1611.02045, Section 3).
+//
+// Convention (Section 3): forward F[f]_p = sum_k f_k e^{-2 pi i p k / M},
+// unnormalised; the inverse carries 1/M, which callers fold into their
+// Fourier-space multiplier.  Output is in natural DFT order p = 0..M-1
+// (p >= M/2 stands for the negative frequency p - M).
+//
+// Layout of one line inside a thread block: the line's M points are shared by
+// Tl = M/E threads; thread t of the line holds E values at positions
+// t + q*Tl (q = 0..E-1) in registers.  The transform is a Stockham
+// (self-sorting) decomposition M = R_1 R_2 ... with every radix R <= E; each
+// stage works in registers (E/R butterflies per thread) and exchanges through
+// shared memory between stages.  The final stage leaves each thread holding
+// exactly the positions t + q*Tl again, so a pointwise Fourier multiplier and
+// the inverse transform's first stage run with no extra exchange.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gpe {
+
+template <typename T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <typename T> using cplx = typename cvec<T>::type;
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// multiply by -i (DIR = -1, forward) or +i (DIR = +1, inverse)
+template <int DIR, typename C> __device__ __forceinline__ C cmul_i(C a) {
+  return DIR < 0 ? cmk<C>(a.y, -a.x) : cmk<C>(-a.y, a.x);
+}
+// a * conj(w) when DIR = +1, a * w when DIR = -1 (w = e^{-2 pi i m / M} table)
+template <int DIR, typename C> __device__ __forceinline__ C ctw(C a, C w) {
+  return DIR < 0 ? cmk<C>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x)
+                 : cmk<C>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs on registers: y_m = sum_r x_r e^{DIR 2 pi i r m / R}
+// (DIR = -1 forward, +1 inverse); computed in place.
+// ---------------------------------------------------------------------------
+template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  C s = cadd(a, b), d = csub(a, b); a = s; b = d;
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+  C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = cmul_i<DIR>(csub(x1, x3));
+  x0 = cadd(a, c); x2 = csub(a, c); x1 = cadd(b, d); x3 = csub(b, d);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft8(C (&x)[8]) {
+  using R = decltype(C::x);
+  const R h = R(0.70710678118654752440);  // cos(pi/4)
+  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  // twiddles e^{DIR 2 pi i m / 8}, m = 1, 2, 3
+  C t1 = DIR < 0 ? cmk<C>(h * (o1.x + o1.y), h * (o1.y - o1.x)) : cmk<C>(h * (o1.x - o1.y), h * (o1.y + o1.x));
+  C t2 = cmul_i<DIR>(o2);
+  C t3 = DIR < 0 ? cmk<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y)) : cmk<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+  x[1] = cadd(e1, t1); x[5] = csub(e1, t1);
+  x[2] = cadd(e2, t2); x[6] = csub(e2, t2);
+  x[3] = cadd(e3, t3); x[7] = csub(e3, t3);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft16(C (&x)[16]) {
+  using R = decltype(C::x);
+  C e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { e[i] = x[2 * i]; o[i] = x[2 * i + 1]; }
+  dft8<DIR>(e);
+  dft8<DIR>(o);
+  // w_m = e^{DIR 2 pi i m / 16} = cos(2 pi m/16) + DIR i sin(2 pi m/16)
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
+  const R cs[8] = {R(1), c1, h, s1, R(0), -s1, -h, -c1};
+  const R sn[8] = {R(0), s1, h, c1, R(1), c1, h, s1};
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    C t;
+    if (m == 0) t = o[0];
+    else if (m == 4) t = cmul_i<DIR>(o[4]);
+    else t = cmk<C>(o[m].x * cs[m] - R(DIR) * o[m].y * sn[m], o[m].y * cs[m] + R(DIR) * o[m].x * sn[m]);
+    x[m] = cadd(e[m], t);
+    x[m + 8] = csub(e[m], t);
+  }
+}
+
+template <int R, int DIR, typename C> __device__ __forceinline__ void dft_small(C (&x)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<DIR>(x[0], x[1]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    dft8<DIR>(x);
+  } else {
+    static_assert(R == 16, "radix must be 1, 2, 4, 8 or 16");
+    dft16<DIR>(x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stockham stages.  SI: functor mapping a line position to a shared-memory
+// element index for this thread's line slot.
+// ---------------------------------------------------------------------------
+template <int M, int E, int NS, int DIR, typename C, typename SI>
+__device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
+  constexpr int Tl = M / E;
+  constexpr int R = (M / NS >= E) ? E : (M / NS);
+  constexpr int NB = E / R;  // butterflies per thread in this stage
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + b * Tl;  // butterfly index, 0 .. M/R - 1
+    C x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[b + r * NB];
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = ctw<DIR>(x[r], __ldg(&tw[(k * r) * (M / (NS * R))]));
+    }
+    dft_small<R, DIR>(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b + r * NB] = x[r];
+  }
+  if constexpr (NS * R < M) {
+    __syncthreads();  // previous readers of sm are done
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + b * Tl;
+      const int k = j % NS;
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[si(base + r * NS)] = v[b + r * NB];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = sm[si(t + q * Tl)];
+    fft_stages<M, E, NS * R, DIR>(v, sm, si, t, tw);
+  }
+}
+
+// Forward (DIR = -1) or inverse-unnormalised (DIR = +1) DFT of one line held
+// as v[q] = f[t + q*Tl]; on return v[q] = F[f][t + q*Tl].  Every thread of the
+// block must call it (it contains __syncthreads()).
+template <int M, int E, int DIR, typename C, typename SI>
+__device__ __forceinline__ void line_dft(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
+  fft_stages<M, E, 1, DIR>(v, sm, si, t, tw);
+}
+
+}  // namespace gpe

@@ -1,0 +1,124 @@
+// gpe_internal.h -- device control block and pass-launch interface shared by
+// the kernel translation units and the C ABI (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+// Number of doubles in one per-iteration log row (matches GPE_LOG_FIELDS).
+constexpr int kLogFields = 12;
+// Max reduction slots per pass.
+constexpr int kMaxMoments = 12;
+
+// Device-resident scalar state of one solve (or of one API call).  Kernels
+// read the scalars they need at entry; the last thread block of each
+// reducing pass writes the reduced moments and runs the scalar logic.
+struct Ctl {
+  // ---- options (set by the host before a solve) ----
+  double tol_res_inf, tol_dE, theta_default, switch_res;
+  int max_iter, max_backtracks, cg, stall_window, max_iter_phase, phase;
+  int lo_phase;  // 1 while running the complex64 phase of a mixed solve
+  // ---- loop state ----
+  int iter;        // n (global over both phases)
+  int iter_phase0; // value of iter when this phase started
+  int done;        // 1 once the loop must stop
+  int status;      // gpe_status of the solve
+  int restart;     // 1: next direction uses beta = 0 (first iteration of a phase)
+  int retract;     // 1: the next H pass first forms phi_{n+1} from (phi_n, p_n)
+  int fallback;    // gradient step taken this iteration
+  int fallbacks, backtracks_total, backtracks;
+  int switch_req;  // complex64 phase asked for the complex128 phase
+  int stop_dE;     // energy criterion met at the last step
+  // ---- per-iterate scalars ----
+  double kin, rot, pot, U0, norm2;      // <phi,-Lap/2 phi>, <phi,-omega Lz phi>, <phi,V phi>, int|phi|^4, ||phi||^2
+  double lam, alpha, E;                 // lambda_n, lambda~_n, E_n
+  double res_inf, res_l2;
+  double rPr, rPr_prev;                 // <r_n, P r_n>, previous
+  double beta, gamma;                   // beta_n, Re<d_n, phi_n>
+  double theta, c, s, inv_np, inv_nrm;  // retraction scalars for the next H pass
+  double dE;
+  double anchor_res; int anchor_iter;   // stall detection (mixed phase)
+  int pad0;
+  // ---- raw sums written by pass finalisers ----
+  double hsum[3][kMaxMoments];  // H passes, per axis
+  double psum[kMaxMoments];     // P_C passes
+  double asum[3][kMaxMoments];  // A p passes, per axis
+  // ---- log ----
+  double* log;
+  int log_cap;
+  int log_len;
+};
+
+enum Pass : int {
+  P_HX = 0,     // x: [retraction] t = A_x f + (V + eta|phi|^2) f
+  P_HMID = 1,   // y/z: t += A_axis f
+  P_C1 = 2,     // x: s = FFT_x(P_V^{1/2} r)
+  P_CFWD = 3,   // y (3D): s = FFT_y s
+  P_CCORE = 4,  // last axis: s = IFFT(FFT(s) / (alpha + |k|^2/2)) / N
+  P_CINV = 5,   // y (3D): s = IFFT_y s
+  P_C3 = 6,     // x: Pr = P_V^{1/2} IFFT_x s (+ solver reductions)
+  P_AX = 7,     // x: p = -Pr + beta p_prev - gamma phi; Parseval moments
+  P_AMID = 8,   // y/z: Parseval moments of A_axis p
+  P_NUM = 9
+};
+
+// Everything a pass kernel needs, passed by value.
+struct PassArgs {
+  int dim, nx, ny, nz;
+  int axis;        // physical axis transformed by this pass
+  int M;           // length along that axis
+  int lpb;         // contiguous passes: lines per block
+  int tx;          // strided passes: tile width in x
+  long long stride;        // strided: element stride along the axis
+  long long outer_stride;  // strided: element stride of the outer index
+  int ntx;         // strided: nx / tx
+  int nblocks;     // grid size
+  int solver;      // 1: inside a solve (uses ctl scalars, solver reductions)
+  int last_axis;   // 1: this pass is the final one of its operator (runs the finaliser)
+  double weight;   // h^d
+  double eta, omega;
+  // device tables, in the kernel's precision (T*), stored as void*
+  const void* xi[3];   // frequencies per axis, DFT order
+  const void* xc[3];   // coordinates per axis
+  const void* tw;      // twiddles e^{-2 pi i m/M}, m < M, for this axis
+  const void* V;       // potential, real
+  // fields (complex, kernel precision)
+  const void* phi;     // phi_n (or phi_{n} before retraction)
+  void* phi_out;       // HX: where phi_{n+1} is written (solver, retract)
+  const void* f;       // operand (API apply_H: f; solver: = phi)
+  void* p;             // direction p (read in HX for retraction, written in AX)
+  void* t;             // H accumulator / H phi
+  void* s;             // P_C workspace (s_hat, then P r)
+  void* r_prev;        // r_{n-1}, overwritten with r_n by P_C3 (solver)
+  const void* r_in;    // API precond input r
+  void* out;           // API output
+  double api_alpha;    // API precond shift (> 0)
+  Ctl* ctl;
+  double* partials;    // [nblocks][kMaxMoments]
+  unsigned int* ticket;
+  unsigned long long cond;  // cudaGraphConditionalHandle (0 = none)
+};
+
+// Launch one pass in precision T (float or double).  Returns cudaSuccess or
+// the launch error.  Defined in gpe_kernels_f32.cu / gpe_kernels_f64.cu.
+cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st);
+
+// Per-group launchers (gpe_k_<prec>_<group>.cu).
+cudaError_t launch_group_f32_h(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f32_c(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f32_a(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_h(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_c(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_a(Pass pass, const PassArgs& a, cudaStream_t st);
+
+// Small elementwise/control kernels (gpe_misc.cu).
+cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st);
+cudaError_t launch_convert_c64_to_c128(const void* src, void* dst, long long n, cudaStream_t st);
+cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t st);
+// ctl->c = 1, s = 0, inv_nrm = 1 / ||phi||, retract = 1 (weighted norm), so
+// that the next H pass normalises phi in place.
+cudaError_t launch_init_norm(int is_double, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st);
+
+}  // namespace gpe

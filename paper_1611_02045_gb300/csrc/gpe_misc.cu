@@ -1,0 +1,87 @@
+// gpe_misc.cu -- pass dispatch and the small elementwise kernels around a
+// solve (precision conversion, initial normalisation).
+#include "gpe_internal.h"
+
+namespace gpe {
+
+cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st) {
+  switch (pass) {
+    case P_HX: case P_HMID: return launch_group_f32_h(pass, a, st);
+    case P_AX: case P_AMID: return launch_group_f32_a(pass, a, st);
+    default: return launch_group_f32_c(pass, a, st);
+  }
+}
+
+cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st) {
+  switch (pass) {
+    case P_HX: case P_HMID: return launch_group_f64_h(pass, a, st);
+    case P_AX: case P_AMID: return launch_group_f64_a(pass, a, st);
+    default: return launch_group_f64_c(pass, a, st);
+  }
+}
+
+__global__ void k_c128_to_c64(const double2* __restrict__ s, float2* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = s[i];
+    d[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void k_c64_to_c128(const float2* __restrict__ s, double2* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = s[i];
+    d[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = (float)s[i];
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_c128_to_c64<<<grid_for(n), 256, 0, st>>>((const double2*)src, (float2*)dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_c64_to_c128(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_c64_to_c128<<<grid_for(n), 256, 0, st>>>((const float2*)src, (double2*)dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t st) {
+  k_d2f<<<grid_for(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+// One block, fixed-order FP64 sum of |phi|^2 (runs once per solve phase).
+template <typename C>
+__global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, long long n, double weight, Ctl* ctl) {
+  __shared__ double sm[32];
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const C v = phi[i];
+    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sm[w];
+    ctl->c = 1.0;
+    ctl->s = 0.0;
+    ctl->inv_np = 0.0;
+    ctl->inv_nrm = 1.0 / sqrt(weight * tot);
+    ctl->retract = 1;
+  }
+}
+
+cudaError_t launch_init_norm(int is_double, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st) {
+  if (is_double) k_init_norm<double2><<<1, 1024, 0, st>>>((const double2*)phi, n, weight, ctl);
+  else k_init_norm<float2><<<1, 1024, 0, st>>>((const float2*)phi, n, weight, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace gpe

@@ -1,0 +1,614 @@
+// gpe_passes.cuh -- the per-axis pass kernels of one PCG_C iteration
+// (arXiv:1611.02045, Algorithm 2 with the operators of Sections 2, 3, 5.5).
+//
+// Each pass streams every point of a field once along one axis: it loads a
+// line (x) or a tile of TX adjacent lines (y, z) into registers, applies a
+// pointwise prologue, a line DFT (gpe_fft.cuh), a Fourier-space multiplier,
+// optionally the inverse DFT, and a pointwise epilogue, then writes the
+// result.  Reductions are accumulated per thread, combined per block in FP64
+// and summed over blocks in a fixed order by the last block to finish, which
+// then runs the scalar step that belongs after that pass (chemical potential,
+// convergence test, Polak-Ribiere coefficient, step size).
+//
+// Pass roles (Pass enum in gpe_internal.h), 2D order per iteration:
+//   HX   : [phi <- (c phi + s p/|p|)/nrm] ; t = (1/2 xi^2 + omega y xi) f + (V + eta|phi|^2) f
+//   HMID : t += (1/2 mu^2 - omega x mu) f   (y)      or  (1/2 zeta^2) f  (z)
+//   C1   : s = FFT_x[ P_V^{1/2} (t - lambda phi) ]
+//   CCORE: s = IFFT_y[ FFT_y(s) / (alpha + |k|^2/2) ] / N
+//   C3   : Pr = P_V^{1/2} IFFT_x[s]; r_prev <- r
+//   AX   : p = -Pr + beta p_prev - gamma phi;  moments of p and of FFT_x p
+//   AMID : moments of FFT_y p
+// (3D inserts HMID for z, CFWD/CINV for y around CCORE on z, AMID for z.)
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gpe_fft.cuh"
+#include "gpe_internal.h"
+
+namespace gpe {
+
+enum StatusCode { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_NOT_CONVERGED = 3, ST_NONFINITE = 4, ST_PRECOND = 5 };
+
+template <int M> struct LineCfg {
+  static constexpr int E = 8;     // values per thread
+  static constexpr int Tl = M / E;  // threads per line
+  static_assert(M >= 8 && (M & (M - 1)) == 0, "M must be a power of two >= 8");
+};
+
+// ---------------------------------------------------------------------------
+// Reductions: K per-thread values -> per-block partial -> last block total.
+// MAXMASK bit k set: slot k is reduced with max instead of sum.
+// Returns true in every thread of the last block, with tot[] valid in
+// thread 0.
+// ---------------------------------------------------------------------------
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ double red_op(double a, double b, int k) {
+  return ((MAXMASK >> k) & 1u) ? fmax(a, b) : a + b;
+}
+
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ void block_reduce(double (&v)[K], double* red_sm) {
+  // blockDim.x is a power of two: either a multiple of 32 or one partial warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int width = blockDim.x < 32 ? (int)blockDim.x : 32;
+  const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    for (int o = width >> 1; o > 0; o >>= 1) v[k] = red_op<K, MAXMASK>(v[k], __shfl_xor_sync(mask, v[k], o), k);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red_sm[warp * K + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double acc = red_sm[k];
+      for (int w = 1; w < nw; ++w) acc = red_op<K, MAXMASK>(acc, red_sm[w * K + k], k);
+      v[k] = acc;
+    }
+  }
+}
+
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], const PassArgs& a, double (&tot)[K]) {
+  __shared__ double red_sm[32 * K];
+  __shared__ int s_last;
+  block_reduce<K, MAXMASK>(v, red_sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.partials[(size_t)blockIdx.x * kMaxMoments + k] = v[k];
+    __threadfence();
+    const unsigned prev = atomicAdd(a.ticket, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = 0.0;  // all slots hold non-negative values or sums
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const volatile double* pb = a.partials + (size_t)b * kMaxMoments;
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = red_op<K, MAXMASK>(w[k], pb[k], k);
+  }
+  block_reduce<K, MAXMASK>(w, red_sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = w[k];
+    *a.ticket = 0u;  // ready for the next pass
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar steps (run by one thread of the last block)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double* log_row(Ctl* c) {
+  return (c->log && c->iter < c->log_cap) ? c->log + (size_t)c->iter * kLogFields : nullptr;
+}
+
+// After the last H pass: energy terms, lambda_n, lambda~_n, E_n (Section 2, eq. Opt_Alpha).
+static __device__ void finalize_H(const PassArgs& a) {
+  Ctl* c = a.ctl;
+  const double w = a.weight;
+  double kin = 0.0, rot = 0.0;
+  for (int ax = 0; ax < a.dim; ++ax) { kin += c->hsum[ax][0]; rot += c->hsum[ax][1]; }
+  c->kin = w * kin;
+  c->rot = w * rot;
+  c->pot = w * c->hsum[0][2];
+  c->U0 = w * c->hsum[0][3];
+  c->norm2 = w * c->hsum[0][4];
+  const double quad = c->kin + c->rot + c->pot;
+  c->lam = quad + a.eta * c->U0;                           // <phi, H phi>
+  c->alpha = c->kin + c->pot + a.eta * c->U0;              // lambda~ (no rotation term)
+  c->E = quad + 0.5 * a.eta * c->U0;
+  if (a.solver) {
+    double* row = log_row(c);
+    if (row) {
+      row[0] = c->iter; row[1] = c->phase; row[2] = c->E; row[3] = c->lam;
+      row[6] = c->alpha;
+      row[4] = row[5] = row[7] = row[8] = row[9] = row[10] = row[11] = 0.0;
+    }
+    if (c->log && c->iter + 1 > c->log_len) c->log_len = (c->iter + 1 < c->log_cap) ? c->iter + 1 : c->log_cap;
+  }
+}
+
+// After C1: residual norms and the stopping rule (eq. Stop_Residual), the
+// iteration cap, the optional energy rule, and (mixed phase) stall detection.
+static __device__ void finalize_C1(const PassArgs& a, const double (&tot)[3]) {
+  Ctl* c = a.ctl;
+  c->res_inf = sqrt(tot[0]);
+  c->res_l2 = sqrt(a.weight * tot[1]);
+  double* row = log_row(c);
+  if (row) { row[4] = c->res_inf; row[5] = c->res_l2; }
+  const int nphase = c->iter - c->iter_phase0;
+  if (!isfinite(c->E) || !isfinite(c->res_inf) || !isfinite(c->lam)) {
+    c->status = ST_NONFINITE; c->done = 1;
+  } else if (tot[2] > 0.0) {
+    c->status = ST_PRECOND; c->done = 1;
+  } else if (c->res_inf < c->tol_res_inf || c->stop_dE) {
+    c->status = ST_OK; c->done = 1;
+  } else if (c->iter >= c->max_iter) {
+    c->status = ST_NOT_CONVERGED; c->done = 1;
+  } else if (c->lo_phase) {
+    if (c->res_inf <= 0.5 * c->anchor_res) { c->anchor_res = c->res_inf; c->anchor_iter = c->iter; }
+    if (c->res_inf < c->switch_res || c->iter - c->anchor_iter >= c->stall_window || nphase >= c->max_iter_phase) {
+      c->switch_req = 1; c->status = ST_NOT_CONVERGED; c->done = 1;
+    }
+  }
+}
+
+// After C3: Polak-Ribiere beta+ (eq. CG:PR), gamma = Re<d, phi>, and the
+// descent check of Section 5.2 (Re<grad E, p> >= 0 -> gradient step).
+// tot: 0 <r,Pr>, 1 Re<r - r_prev, Pr>, 2 Re<Pr,phi>, 3 Re<p_prev,phi>,
+//      4 Re<r,p_prev>, 5 Re<r,phi>
+static __device__ void finalize_C3(const PassArgs& a, const double (&tot)[6]) {
+  Ctl* c = a.ctl;
+  const double w = a.weight;
+  const double rPr = w * tot[0];
+  double beta = 0.0;
+  if (!c->restart && c->cg) beta = fmax(w * tot[1] / c->rPr_prev, 0.0);
+  const double Prphi = w * tot[2], pphi = w * tot[3], rp = w * tot[4], rphi = w * tot[5];
+  double gamma = -Prphi + beta * pphi;
+  // Re<H phi, p> = Re<r, d> - gamma Re<r, phi> + lambda gamma (1 - ||phi||^2)
+  const double desc = -rPr + beta * rp - gamma * rphi + c->lam * gamma * (1.0 - c->norm2);
+  c->fallback = 0;
+  if (desc >= 0.0) {
+    c->fallback = 1; c->fallbacks += 1;
+    beta = 0.0; gamma = -Prphi;
+  }
+  c->beta = beta; c->gamma = gamma; c->rPr = rPr;
+  c->rPr_prev = rPr;
+  double* row = log_row(c);
+  if (row) { row[7] = beta; row[10] = c->fallback; }
+}
+
+// Energy change along the geodesic, exact trigonometric polynomial (reading R6).
+__device__ __forceinline__ double delta_E(double th, double R, double aqq, double lam, double eta,
+                                          double U0, double U1, double V2, double UW, double VW, double W2) {
+  double s, cth;
+  sincos(th, &s, &cth);
+  const double s2 = s * s, c2 = cth * cth;
+  return 2.0 * cth * s * R + s2 * (aqq - lam) +
+         0.5 * eta * (s2 * s2 * (U0 + W2) + c2 * s2 * (4.0 * V2 + 2.0 * UW) + 4.0 * cth * s * s2 * (VW - U1));
+}
+
+// After the last A pass: step size by the model minimiser (eq. theta_opt,
+// reading R4) with energy-decrease backtracking (Section 5.1), then the
+// retraction scalars for the next H pass.
+// asum[0]: 0 Re<H phi,p>, 1 <p,A_x p>+<p,V p>, 2 |p|^2, 3 u v, 4 v^2, 5 u w,
+//          6 v w, 7 w^2, 8 v    (u = |phi|^2, v = Re(conj(phi) p), w = |p|^2)
+// asum[ax>0][1]: <p, A_ax p>
+static __device__ void finalize_A(const PassArgs& a) {
+  Ctl* c = a.ctl;
+  const double w = a.weight;
+  const double* s0 = c->asum[0];
+  const double W1 = w * s0[2];
+  const double inv = 1.0 / sqrt(W1);
+  double app = s0[1];
+  for (int ax = 1; ax < a.dim; ++ax) app += c->asum[ax][1];
+  const double R = w * s0[0] * inv;
+  const double aqq = w * app * inv * inv;
+  const double U1 = w * s0[3] * inv, V2 = w * s0[4] * inv * inv, UW = w * s0[5] * inv * inv;
+  const double VW = w * s0[6] * inv * inv * inv, W2 = w * s0[7] * inv * inv * inv * inv;
+  const double rho = w * s0[8] * inv;
+  const double eta = a.eta, lam = c->lam, U0 = c->U0;
+  const double curv = aqq + eta * UW + 2.0 * eta * V2 - lam;
+  double th = (curv > 0.0) ? -R / curv : c->theta_default;
+  double dE = delta_E(th, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
+  int bt = 0;
+  while (!(dE < 0.0) && bt < c->max_backtracks) {
+    th *= 0.5; ++bt;
+    dE = delta_E(th, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
+  }
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  const double nrm2 = cs * cs * c->norm2 + 2.0 * cs * sn * rho + sn * sn;
+  c->theta = th; c->c = cs; c->s = sn; c->inv_np = inv; c->inv_nrm = 1.0 / sqrt(nrm2);
+  c->dE = dE; c->backtracks = bt; c->backtracks_total += bt;
+  double* row = log_row(c);
+  if (row) { row[8] = th; row[9] = dE; row[11] = bt; }
+  c->retract = 1;
+  c->restart = 0;
+  c->iter += 1;
+  if (c->tol_dE > 0.0 && fabs(dE) <= c->tol_dE) c->stop_dE = 1;
+  if (!isfinite(dE) || !isfinite(th)) { c->status = ST_NONFINITE; c->done = 1; }
+}
+
+__device__ __forceinline__ void set_loop_condition(const PassArgs& a, int keep_going) {
+  if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, keep_going ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Multipliers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ const T* tab(const void* p) { return static_cast<const T*>(p); }
+
+// ---------------------------------------------------------------------------
+// Contiguous (x) passes.  Block = lpb lines x Tl threads; tid = t + Tl*l.
+// ---------------------------------------------------------------------------
+// Max threads per block: 512 in single precision, 256 in double (register budget).
+template <typename T> struct MaxThreads { static constexpr int value = sizeof(T) == 8 ? 256 : 512; };
+
+template <typename T, int M, int ROLE>
+__global__ void __launch_bounds__(MaxThreads<T>::value) pass_x(PassArgs a) {
+  using C = cplx<T>;
+  constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
+  constexpr int LS = M + M / 16;  // padded line stride in shared memory
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  Ctl* ctl = a.ctl;
+  if (a.solver && ctl->done) return;
+
+  const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
+  const long long line = (long long)blockIdx.x * a.lpb + l;
+  const long long base = line * M;
+  const int iy = (int)(line % a.ny);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const T* __restrict__ xi = tab<T>(a.xi[0]);
+  const T* __restrict__ V = tab<T>(a.V);
+  auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
+  const T invM = T(1) / T(M);
+
+  C v[E];
+  if constexpr (ROLE == P_HX) {
+    // ---- H_phi f, x part, plus the real-space terms --------------------------------
+    const C* __restrict__ phi = static_cast<const C*>(a.phi);
+    const C* __restrict__ f = static_cast<const C*>(a.f ? a.f : a.phi);
+    C ph[E];
+    T vv[E];
+    const bool retract = a.solver && ctl->retract;
+    const T cc = T(retract ? ctl->c * ctl->inv_nrm : 1.0);
+    const T ss = T(retract ? ctl->s * ctl->inv_np * ctl->inv_nrm : 0.0);
+    const C* __restrict__ p = static_cast<const C*>(a.p);
+    C* __restrict__ phi_out = static_cast<C*>(a.phi_out);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      vv[q] = V[g];
+      C x = phi[g];
+      if (retract) {
+        const C pq = p[g];
+        x = cmk<C>(cc * x.x + ss * pq.x, cc * x.y + ss * pq.y);
+        phi_out[g] = x;
+      }
+      ph[q] = x;
+      v[q] = (a.f && !a.solver) ? f[g] : x;
+    }
+    line_dft<M, E, -1>(v, sm, si, t, tw);
+    const T y = tab<T>(a.xc[1])[iy];
+    const T om = T(a.omega);
+    T akin = 0, arot = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xi[t + q * Tl];
+      const T mk = T(0.5) * k * k, mr = om * y * k;
+      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+      akin += mk * a2; arot += mr * a2;
+      v[q] = cscale(v[q], (mk + mr) * invM);
+    }
+    line_dft<M, E, +1>(v, sm, si, t, tw);
+    C* __restrict__ tout = static_cast<C*>(a.t);
+    const T eta = T(a.eta);
+    T apot = 0, au2 = 0, an2 = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      const T u = ph[q].x * ph[q].x + ph[q].y * ph[q].y;
+      const T m = vv[q] + eta * u;
+      const C fq = (a.f && !a.solver) ? f[g] : ph[q];  // the operand f (re-read in API mode)
+      tout[g] = cmk<C>(v[q].x + m * fq.x, v[q].y + m * fq.y);
+      apot += vv[q] * u; au2 += u * u; an2 += u;
+    }
+    double acc[5] = {double(akin) * double(invM), double(arot) * double(invM), double(apot), double(au2), double(an2)};
+    double tot[5];
+    if (grid_reduce<5, 0u>(acc, a, tot) && threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) ctl->hsum[0][k] = tot[k];
+    }
+  } else if constexpr (ROLE == P_C1) {
+    // ---- s = FFT_x[P_V^{1/2} r], r = H phi - lambda phi (solver) or r_in (API) ----
+    const C* __restrict__ phi = static_cast<const C*>(a.phi);
+    const C* __restrict__ rin = static_cast<const C*>(a.solver ? a.t : a.r_in);
+    const T lam = T(a.solver ? ctl->lam : 0.0);
+    const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
+    const T alpha = T(alpha_d);
+    const T eta = T(a.eta);
+    T rmax = 0, r2 = 0, bad = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      const C ph = phi[g];
+      C r = rin[g];
+      if (a.solver) r = cmk<C>(r.x - lam * ph.x, r.y - lam * ph.y);
+      const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+      bad += (den > T(0)) ? T(0) : T(1);
+      const T a2 = r.x * r.x + r.y * r.y;
+      rmax = fmax(rmax, a2); r2 += a2;
+      v[q] = cscale(r, T(1) / sqrt(den));
+    }
+    line_dft<M, E, -1>(v, sm, si, t, tw);
+    C* __restrict__ sout = static_cast<C*>(a.s);
+#pragma unroll
+    for (int q = 0; q < E; ++q) sout[base + t + q * Tl] = v[q];
+    if (a.solver) {
+      double acc[3] = {double(rmax), double(r2), double(bad)};
+      double tot[3];
+      if (grid_reduce<3, 1u>(acc, a, tot) && threadIdx.x == 0) finalize_C1(a, tot);
+    }
+  } else if constexpr (ROLE == P_C3) {
+    // ---- Pr = P_V^{1/2} IFFT_x[s] (the 1/N is applied in the core pass) ----
+    const C* __restrict__ phi = static_cast<const C*>(a.phi);
+    C* __restrict__ sbuf = static_cast<C*>(a.s);
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = sbuf[base + t + q * Tl];
+    line_dft<M, E, +1>(v, sm, si, t, tw);
+    const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
+    const T alpha = T(alpha_d);
+    const T eta = T(a.eta);
+    if (!a.solver) {
+      C* __restrict__ out = static_cast<C*>(a.out);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const long long g = base + t + q * Tl;
+        const C ph = phi[g];
+        const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+        out[g] = cscale(v[q], T(1) / sqrt(den));
+      }
+      return;
+    }
+    const C* __restrict__ Hphi = static_cast<const C*>(a.t);
+    C* __restrict__ rprev = static_cast<C*>(a.r_prev);
+    const C* __restrict__ pprev = static_cast<const C*>(a.p);
+    const T lam = T(ctl->lam);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      const C ph = phi[g];
+      const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+      const C Pr = cscale(v[q], T(1) / sqrt(den));
+      sbuf[g] = Pr;
+      const C h = Hphi[g];
+      const C r = cmk<C>(h.x - lam * ph.x, h.y - lam * ph.y);
+      const C ro = rprev[g];
+      const C pp = pprev[g];
+      a0 += r.x * Pr.x + r.y * Pr.y;
+      a1 += (r.x - ro.x) * Pr.x + (r.y - ro.y) * Pr.y;
+      a2 += Pr.x * ph.x + Pr.y * ph.y;
+      a3 += pp.x * ph.x + pp.y * ph.y;
+      a4 += r.x * pp.x + r.y * pp.y;
+      a5 += r.x * ph.x + r.y * ph.y;
+      rprev[g] = r;
+    }
+    double acc[6] = {double(a0), double(a1), double(a2), double(a3), double(a4), double(a5)};
+    double tot[6];
+    if (grid_reduce<6, 0u>(acc, a, tot) && threadIdx.x == 0) finalize_C3(a, tot);
+  } else if constexpr (ROLE == P_AX) {
+    // ---- p = -Pr + beta p_prev - gamma phi ; moments for the step size ----
+    const C* __restrict__ phi = static_cast<const C*>(a.phi);
+    const C* __restrict__ Pr = static_cast<const C*>(a.s);
+    const C* __restrict__ Hphi = static_cast<const C*>(a.t);
+    C* __restrict__ pbuf = static_cast<C*>(a.p);
+    const T beta = T(ctl->beta), gamma = T(ctl->gamma);
+    T aR = 0, aV = 0, aW1 = 0, aUV = 0, aV2 = 0, aUW = 0, aVW = 0, aW2 = 0, aRho = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      const C ph = phi[g], pr = Pr[g], pp = pbuf[g], h = Hphi[g];
+      const C pn = cmk<C>(-pr.x + beta * pp.x - gamma * ph.x, -pr.y + beta * pp.y - gamma * ph.y);
+      pbuf[g] = pn;
+      v[q] = pn;
+      const T u = ph.x * ph.x + ph.y * ph.y;
+      const T vr = ph.x * pn.x + ph.y * pn.y;
+      const T wq = pn.x * pn.x + pn.y * pn.y;
+      aR += h.x * pn.x + h.y * pn.y;
+      aV += V[g] * wq;
+      aW1 += wq; aUV += u * vr; aV2 += vr * vr; aUW += u * wq; aVW += vr * wq; aW2 += wq * wq; aRho += vr;
+    }
+    line_dft<M, E, -1>(v, sm, si, t, tw);
+    const T y = tab<T>(a.xc[1])[iy];
+    const T om = T(a.omega);
+    T akr = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xi[t + q * Tl];
+      akr += (T(0.5) * k * k + om * y * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
+    }
+    double acc[9] = {double(aR), double(aV) + double(akr) * double(invM), double(aW1), double(aUV), double(aV2),
+                     double(aUW), double(aVW), double(aW2), double(aRho)};
+    double tot[9];
+    if (grid_reduce<9, 0u>(acc, a, tot) && threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) ctl->asum[0][k] = tot[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strided (y, z) passes.  Block = tx columns x Tl threads; tid = c + tx*t.
+// ---------------------------------------------------------------------------
+template <typename T, int M, int ROLE>
+__global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
+  using C = cplx<T>;
+  constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  Ctl* ctl = a.ctl;
+  const bool is_loop_tail = (ROLE == P_AMID) && a.last_axis;
+  if (a.solver && ctl->done) {
+    if (is_loop_tail && blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(a, 0);
+    return;
+  }
+  const int tx = a.tx;
+  const int c = threadIdx.x % tx, t = threadIdx.x / tx;
+  const int xt = blockIdx.x % a.ntx;
+  const long long outer = blockIdx.x / a.ntx;
+  const int ix = xt * tx + c;
+  const long long base = outer * a.outer_stride + ix;
+  const long long st = a.stride;
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  auto si = [tx, c](int pos) { return pos * tx + c; };
+  const T* __restrict__ xia = tab<T>(a.xi[a.axis]);
+  const T invM = T(1) / T(M);
+
+  C v[E];
+  if constexpr (ROLE == P_HMID) {
+    const C* __restrict__ f = static_cast<const C*>((a.f && !a.solver) ? a.f : a.phi);
+    const C* tb = static_cast<const C*>(a.t);
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = f[base + (t + q * Tl) * st];
+    line_dft<M, E, -1>(v, sm, si, t, tw);
+    const T om = T(a.omega);
+    const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
+    const T rs = (a.axis == 1) ? -om * x : T(0);  // rotation symbol factor: -omega x mu (y) ; none for z
+    T akin = 0, arot = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xia[t + q * Tl];
+      const T mk = T(0.5) * k * k, mr = rs * k;
+      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+      akin += mk * a2; arot += mr * a2;
+      v[q] = cscale(v[q], (mk + mr) * invM);
+    }
+    line_dft<M, E, +1>(v, sm, si, t, tw);
+    C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: final pass writes the caller's buffer
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + (t + q * Tl) * st;
+      dst[g] = cadd(tb[g], v[q]);
+    }
+    double acc[2] = {double(akin) * double(invM), double(arot) * double(invM)};
+    double tot[2];
+    if (grid_reduce<2, 0u>(acc, a, tot) && threadIdx.x == 0) {
+      ctl->hsum[a.axis][0] = tot[0];
+      ctl->hsum[a.axis][1] = tot[1];
+      if (a.last_axis) finalize_H(a);
+    }
+  } else if constexpr (ROLE == P_CFWD || ROLE == P_CINV || ROLE == P_CCORE) {
+    C* __restrict__ sb = static_cast<C*>(a.s);
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = sb[base + (t + q * Tl) * st];
+    if constexpr (ROLE == P_CINV) {
+      line_dft<M, E, +1>(v, sm, si, t, tw);
+    } else {
+      line_dft<M, E, -1>(v, sm, si, t, tw);
+    }
+    if constexpr (ROLE == P_CCORE) {
+      // (alpha + |k|^2 / 2)^{-1} / N on the full frequency grid (eq. PDelta)
+      const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
+      const T alpha = T(alpha_d);
+      const T invN = T(1.0 / ((double)a.nx * a.ny * (a.dim == 3 ? a.nz : 1)));
+      const T kx = tab<T>(a.xi[0])[ix];
+      T kother = 0;
+      if (a.dim == 3) {
+        // axis == 2 (z) here; y index is the outer index
+        const T ky = tab<T>(a.xi[1])[outer];
+        kother = ky * ky;
+      }
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const T k = xia[t + q * Tl];
+        const T den = alpha + T(0.5) * (kx * kx + kother + k * k);
+        v[q] = cscale(v[q], invN / den);
+      }
+      line_dft<M, E, +1>(v, sm, si, t, tw);
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) sb[base + (t + q * Tl) * st] = v[q];
+  } else if constexpr (ROLE == P_AMID) {
+    const C* __restrict__ pb = static_cast<const C*>(a.p);
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = pb[base + (t + q * Tl) * st];
+    line_dft<M, E, -1>(v, sm, si, t, tw);
+    const T om = T(a.omega);
+    const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
+    const T rs = (a.axis == 1) ? -om * x : T(0);
+    T akr = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xia[t + q * Tl];
+      akr += (T(0.5) * k * k + rs * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
+    }
+    double acc[1] = {double(akr) * double(invM)};
+    double tot[1];
+    if (grid_reduce<1, 0u>(acc, a, tot) && threadIdx.x == 0) {
+      ctl->asum[a.axis][1] = tot[0];
+      if (a.last_axis) {
+        finalize_A(a);
+        set_loop_condition(a, ctl->done ? 0 : 1);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch over M
+// ---------------------------------------------------------------------------
+template <typename T, int M, int ROLE>
+cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
+  using C = cplx<T>;
+  constexpr int Tl = LineCfg<M>::Tl;
+  constexpr bool contig = (ROLE == P_HX || ROLE == P_C1 || ROLE == P_C3 || ROLE == P_AX);
+  int threads, smem;
+  if constexpr (contig) {
+    threads = Tl * a.lpb;
+    smem = a.lpb * (M + M / 16) * (int)sizeof(C);
+  } else {
+    threads = Tl * a.tx;
+    smem = M * a.tx * (int)sizeof(C);
+  }
+  void (*kern)(PassArgs);
+  if constexpr (contig) kern = pass_x<T, M, ROLE>;
+  else kern = pass_s<T, M, ROLE>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<a.nblocks, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int ROLE>
+cudaError_t launch_role(const PassArgs& a, cudaStream_t st) {
+  switch (a.M) {
+    case 8: return launch_one<T, 8, ROLE>(a, st);
+    case 16: return launch_one<T, 16, ROLE>(a, st);
+    case 32: return launch_one<T, 32, ROLE>(a, st);
+    case 64: return launch_one<T, 64, ROLE>(a, st);
+    case 128: return launch_one<T, 128, ROLE>(a, st);
+    case 256: return launch_one<T, 256, ROLE>(a, st);
+    case 512: return launch_one<T, 512, ROLE>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gpe

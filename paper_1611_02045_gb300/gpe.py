@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libgpe (include/gpe.h): argument marshalling only.
+
+Every computation runs in libgpe's CUDA kernels.  There is no CPU fallback:
+if libgpe.so is missing or cannot be loaded, every call raises.
+
+Field arguments may be torch tensors (device or host), numpy arrays (host) or
+raw integer addresses.  PyTorch is used only to hold device memory and to
+provide the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libgpe.so"
+
+GPE_OK, GPE_ERR_ARG, GPE_ERR_CUDA, GPE_ERR_NOT_CONVERGED, GPE_ERR_NONFINITE, GPE_ERR_PRECOND, \
+    GPE_ERR_TIMEOUT, GPE_ERR_UNSUPPORTED = range(8)
+GPE_FP64, GPE_MIXED = 0, 1
+GPE_LOG_FIELDS = 12
+LOG_COLUMNS = ("n", "phase", "E", "lam", "res_inf", "res_l2", "alpha", "beta", "theta", "dE",
+               "fallback", "backtracks")
+STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "not_converged", 4: "nonfinite", 5: "precond",
+                6: "timeout", 7: "unsupported"}
+
+
+class gpe_problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3), ("eta", C.c_double),
+                ("omega", C.c_double), ("prec", C.c_int)]
+
+
+class gpe_solve_opts(C.Structure):
+    _fields_ = [("tol_res_inf", C.c_double), ("tol_dE", C.c_double), ("max_iter", C.c_int),
+                ("theta_default", C.c_double), ("max_backtracks", C.c_int), ("cg", C.c_int),
+                ("stall_window", C.c_int), ("switch_res", C.c_double), ("max_iter_lo", C.c_int),
+                ("use_graph", C.c_int)]
+
+
+class gpe_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("iters_lo", C.c_int), ("fallbacks", C.c_int),
+                ("backtracks", C.c_int), ("E", C.c_double), ("lambda_", C.c_double), ("res_inf", C.c_double),
+                ("res_l2", C.c_double), ("log_cap", C.c_int), ("log_len", C.c_int),
+                ("log", C.POINTER(C.c_double))]
+
+
+class GpeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libgpe status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_precond",
+            "gpe_energy", "gpe_pcg_solve", "gpe_last_error")
+
+
+def lib():
+    """Load libgpe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"{_LIB_PATH} not built; run paper_1611_02045_gb300.build.build()")
+        L = C.CDLL(str(_LIB_PATH))
+        vp = C.c_void_p
+        L.gpe_solve_opts_default.argtypes = [C.POINTER(gpe_solve_opts)]
+        L.gpe_create.argtypes = [C.POINTER(gpe_problem), vp, vp, C.POINTER(vp)]
+        L.gpe_destroy.argtypes = [vp]
+        L.gpe_apply_H.argtypes = [vp, vp, vp, vp]
+        L.gpe_precond.argtypes = [vp, vp, vp, C.c_double, vp]
+        L.gpe_energy.argtypes = [vp, vp, C.POINTER(C.c_double)]
+        L.gpe_pcg_solve.argtypes = [vp, vp, C.POINTER(gpe_solve_opts), C.POINTER(gpe_report)]
+        L.gpe_last_error.argtypes = [vp]
+        L.gpe_last_error.restype = C.c_char_p
+        for name in EXPORTED:
+            if name != "gpe_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _addr(x):
+    """Address of a tensor / array / integer pointer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("field tensors must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("field arrays must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported field type {type(x)}")
+
+
+def solve_opts_default():
+    o = gpe_solve_opts()
+    lib().gpe_solve_opts_default(C.byref(o))
+    return o
+
+
+class Context:
+    """Owns one gpe_ctx.  Mirrors the C entry points by name."""
+
+    def __init__(self, n, L, eta, omega, V, prec=GPE_FP64, stream=None):
+        L_ = lib()
+        p = gpe_problem()
+        p.dim = len(n)
+        for i in range(3):
+            p.n[i] = int(n[i]) if i < len(n) else 1
+            p.L[i] = float(L[i]) if i < len(L) else 1.0
+        p.eta, p.omega, p.prec = float(eta), float(omega), int(prec)
+        self.n, self.L, self.prec, self.dim = tuple(n), tuple(L), int(prec), len(n)
+        self._V = V  # keep alive during create
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            self._V = V
+        ctx = C.c_void_p()
+        st = _stream_handle(stream)
+        s = L_.gpe_create(C.byref(p), _addr(V), st, C.byref(ctx))
+        if s != GPE_OK:
+            raise GpeError(s, L_.gpe_last_error(None).decode())
+        self._ctx = ctx
+
+    def _check(self, s):
+        if s != GPE_OK:
+            raise GpeError(s, lib().gpe_last_error(self._ctx).decode())
+        return s
+
+    def apply_H(self, phi, f, out):
+        return self._check(lib().gpe_apply_H(self._ctx, _addr(phi), _addr(f), _addr(out)))
+
+    def precond(self, phi, r, alpha, out):
+        return self._check(lib().gpe_precond(self._ctx, _addr(phi), _addr(r), float(alpha), _addr(out)))
+
+    def energy(self, phi):
+        out = (C.c_double * 8)()
+        self._check(lib().gpe_energy(self._ctx, _addr(phi), out))
+        keys = ("kin", "pot", "int", "rot", "total", "lam", "lam_tilde", "norm2")
+        return dict(zip(keys, list(out)))
+
+    def pcg_solve(self, phi_inout, opts=None, log_cap=0, check=False):
+        """Run the solver in place on phi_inout (complex128, host or device).
+        Returns a dict with the report and, if log_cap > 0, the per-iteration log."""
+        if opts is None:
+            opts = solve_opts_default()
+        rep = gpe_report()
+        logbuf = None
+        if log_cap > 0:
+            logbuf = np.zeros((log_cap, GPE_LOG_FIELDS), dtype=np.float64)
+            rep.log_cap = log_cap
+            rep.log = logbuf.ctypes.data_as(C.POINTER(C.c_double))
+        s = lib().gpe_pcg_solve(self._ctx, _addr(phi_inout), C.byref(opts), C.byref(rep))
+        if s in (GPE_ERR_ARG, GPE_ERR_CUDA) or (check and s != GPE_OK):
+            self._check(s)
+        out = dict(status=rep.status, status_name=STATUS_NAMES.get(rep.status), iters=rep.iters,
+                   iters_lo=rep.iters_lo, fallbacks=rep.fallbacks, backtracks=rep.backtracks, E=rep.E,
+                   lam=rep.lambda_, res_inf=rep.res_inf, res_l2=rep.res_l2)
+        if logbuf is not None:
+            out["log"] = logbuf[: rep.log_len].copy()
+        return out
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().gpe_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream

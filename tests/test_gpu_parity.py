@@ -1,0 +1,288 @@
+"""GPU (libgpe CUDA kernels, through the C ABI) against the FP64 CPU oracle on
+identical seeded inputs.
+
+Tolerances
+  * complex128 operators: max|gpu - oracle| <= 1e-12 max|oracle| (FFT round-off
+    in FP64 is ~ eps log2(M) ~ 1e-15 of the largest Fourier-space term, times
+    the largest multiplier |k|^2/2 relative to the result's scale);
+  * complex64 operators: 2e-5 relative (FP32 transforms: eps32 ~ 6e-8 times
+    log2(M) and the same multiplier ratio);
+  * FP64 solver: per-iterate E_n to rel 1e-12 and phase-aligned phi_n to
+    relative L2 1e-9 over the first 20 iterations; converged E to rel 1e-10;
+  * mixed solver: converged E to rel 1e-7 and ||r||_inf < 1e-8.
+"""
+import numpy as np
+import pytest
+
+from oracle import gpe_oracle as O
+from paper_1611_02045_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G(built_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_02045_gb300 import gpe
+    return gpe
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def phase_aligned_rel_l2(a, b):
+    """min over global phases of ||a e^{i t} - b|| / ||b||."""
+    z = np.vdot(a, b)
+    a2 = a * (z / abs(z))
+    return float(np.linalg.norm(a2 - b) / np.linalg.norm(b))
+
+
+def make(n, L, eta, omega, V, prec, G):
+    return G.Context(n, L, eta, omega, V, prec=prec)
+
+
+GRIDS = [((8, 8), (2.0, 2.0)), ((16, 32), (3.0, 4.0)), ((64, 64), (8.0, 8.0)), ((256, 256), (16.0, 16.0)),
+         ((8, 16, 8), (2.0, 2.0, 2.0)), ((32, 32, 32), (6.0, 6.0, 6.0)), ((16, 64, 32), (4.0, 6.0, 5.0)),
+         ((128, 128, 128), (8.0, 8.0, 8.0)), ((512, 512), (16.0, 16.0))]
+
+
+def _fields(n, L, smooth):
+    if smooth:
+        phi = I.phi_d(n, L, 0.6) if len(n) == 2 else I.normalise(
+            I.anisotropic_gaussian(n, L, [1.0, 1.0, 2.0]) * (1 + 0.5 * I.mesh(n, L)[0]), n, L)
+        f = phi * (1 + 0.05 * I.random_field(7, n, L))
+    else:
+        phi, f = I.random_field(1, n, L), I.random_field(2, n, L)
+    return phi, f
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_apply_H_matches_oracle(G, n, L, prec):
+    V = I.harmonic(n, L, [1.0, 1.0, 2.0][: len(n)])
+    eta, om = 37.0, 0.7
+    po = O.Problem(n, L, eta, om, V)
+    for smooth in (False, True):
+        phi, f = _fields(n, L, smooth)
+        dt = torch.complex128 if prec == 0 else torch.complex64
+        ph_d, f_d = dev(phi, dt), dev(f, dt)
+        out = torch.empty_like(f_d)
+        with make(n, L, eta, om, V, prec, G) as ctx:
+            ctx.apply_H(ph_d, f_d, out)
+            got = host(out)
+        # oracle on exactly the values the GPU saw
+        want = O.apply_H(po, host(ph_d), host(f_d))
+        tol = 1e-12 if prec == 0 else 2e-5
+        assert relmax(got, want) < tol, (smooth, relmax(got, want))
+
+
+@pytest.mark.parametrize("n,L", GRIDS[:7])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_precond_matches_oracle(G, n, L, prec):
+    V = I.harmonic(n, L)
+    eta, om = 23.0, 0.4
+    po = O.Problem(n, L, eta, om, V)
+    phi, r = _fields(n, L, False)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    ph_d, r_d = dev(phi, dt), dev(r, dt)
+    out = torch.empty_like(r_d)
+    tol = 1e-12 if prec == 0 else 2e-5
+    with make(n, L, eta, om, V, prec, G) as ctx:
+        ctx.precond(ph_d, r_d, 1.3, out)
+        assert relmax(host(out), O.precond_C(po, host(ph_d), host(r_d), 1.3)) < tol
+        # alpha <= 0: the adaptive shift lambda~(phi) of eq. Opt_Alpha
+        ctx.precond(ph_d, r_d, 0.0, out)
+        a = O.lambda_tilde(po, host(ph_d))
+        assert relmax(host(out), O.precond_C(po, host(ph_d), host(r_d), a)) < tol
+        # out aliasing r
+        ctx.precond(ph_d, r_d, 1.3, r_d)
+        assert relmax(host(r_d), O.precond_C(po, host(ph_d), r.astype(host(ph_d).dtype), 1.3)) < tol * 10
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_energy_matches_oracle(G, n, L, prec):
+    V = I.harmonic(n, L, [1.0, 1.0, 2.0][: len(n)])
+    eta, om = 51.0, 0.8
+    po = O.Problem(n, L, eta, om, V)
+    phi, _ = _fields(n, L, True)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    ph_d = dev(phi, dt)
+    with make(n, L, eta, om, V, prec, G) as ctx:
+        e = ctx.energy(ph_d)
+    ph = host(ph_d)
+    w = O.energy_parts(po, ph)
+    tol = 1e-12 if prec == 0 else 2e-6
+    for k in ("kin", "pot", "int", "rot", "total"):
+        assert abs(e[k] - w[k]) <= tol * (abs(w["total"]) + abs(w[k])), k
+    assert abs(e["lam"] - O.chemical_potential(po, ph)) <= tol * abs(e["lam"])
+    assert abs(e["lam_tilde"] - O.lambda_tilde(po, ph)) <= tol * abs(e["lam_tilde"])
+    assert abs(e["norm2"] - O.norm(po, ph) ** 2) <= tol
+
+
+def test_hermitian_and_vortex_eigenfunction_on_gpu(G):
+    n, L = (64, 64), (8.0, 8.0)
+    V = I.harmonic(n, L)
+    b = I.normalise(I.phi_b(n, L), n, L)
+    with make(n, L, 0.0, 0.3, V, 0, G) as ctx:
+        out = torch.empty_like(dev(b))
+        ctx.apply_H(dev(b), dev(b), out)
+        assert np.max(np.abs(host(out) - 1.7 * b)) < 1e-11
+        f, g, phi = (I.random_field(s, n, L) for s in (3, 4, 5))
+        hf, hg = torch.empty_like(dev(f)), torch.empty_like(dev(f))
+        ctx.apply_H(dev(phi), dev(f), hf)
+        ctx.apply_H(dev(phi), dev(g), hg)
+        a = np.vdot(g, host(hf))
+        c = np.conj(np.vdot(f, host(hg)))
+        assert abs(a - c) < 1e-12 * abs(a)
+
+
+# ------------------------------------------------------------------ solver
+def _workload_problem(name):
+    w = I.workload(name)
+    return w, O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_pcg_per_iterate_parity_fp64(G, use_graph):
+    """Same seeded phi_0, FP64: E_n (rel 1e-12) and phi_n (phase-aligned L2 1e-9)
+    over the first 20 iterations; beta_n, theta_n and the discrete decisions agree."""
+    w, po = _workload_problem("c64_2d")
+    K = 20
+    ophi, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions(max_iter=K), keep_iterates=tuple(range(K + 1)))
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 0, G) as ctx:
+        for k in (1, 2, 5, 10, K):
+            phi = dev(w["phi0"])
+            o = G.solve_opts_default()
+            o.max_iter = k
+            o.use_graph = use_graph
+            rep = ctx.pcg_solve(phi, o, log_cap=64)
+            assert rep["iters"] == k and rep["status"] == G.GPE_ERR_NOT_CONVERGED
+            assert phase_aligned_rel_l2(host(phi), orep["iterates"][k]) < 1e-9, k
+        log = rep["log"]
+    assert log.shape[0] == K + 1
+    for n_ in range(K + 1):
+        e = orep["log"][n_]
+        assert abs(log[n_, 2] - e["E"]) <= 1e-12 * abs(e["E"]), n_
+        assert abs(log[n_, 3] - e["lam"]) <= 1e-12 * abs(e["lam"]), n_
+        # r = H phi - lambda phi carries absolute FP64 noise ~ eps |lambda| max|phi|
+        assert abs(log[n_, 4] - e["res_inf"]) <= 1e-9 * e["res_inf"] + 1e-13 * abs(e["lam"]), n_
+        if n_ < K:
+            assert abs(log[n_, 6] - e["alpha"]) <= 1e-12 * abs(e["alpha"])
+            assert abs(log[n_, 7] - e["beta"]) <= 1e-8 * max(abs(e["beta"]), 1e-3)
+            assert abs(log[n_, 8] - e["theta"]) <= 1e-8 * abs(e["theta"])
+            assert int(log[n_, 10]) == int(e["fallback"]) and int(log[n_, 11]) == e["backtracks"]
+
+
+def test_pcg_converged_fp64_matches_oracle(G):
+    w, po = _workload_problem("c64_2d")
+    ophi, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions())
+    assert orep["status"] == "converged"
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 0, G) as ctx:
+        phi = dev(w["phi0"])
+        rep = ctx.pcg_solve(phi, check=True)
+    assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
+    assert abs(rep["E"] - orep["E"]) <= 1e-10 * abs(orep["E"])
+    # the oracle's own residual of the GPU's answer
+    ph = host(phi)
+    r = O.apply_H(po, ph, ph) - O.chemical_potential(po, ph) * ph
+    assert np.max(np.abs(r)) < 1.01e-8
+    assert abs(O.energy(po, ph) - rep["E"]) <= 1e-12 * abs(rep["E"])
+
+
+def test_pcg_mixed_refinement_reaches_fp64_answer(G):
+    w, po = _workload_problem("c64_2d")
+    ophi, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions())
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 1, G) as ctx:
+        phi = dev(w["phi0"])
+        rep = ctx.pcg_solve(phi, check=True, log_cap=4096)
+    assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
+    assert rep["iters_lo"] > 0 and rep["iters"] > rep["iters_lo"]
+    assert abs(rep["E"] - orep["E"]) <= 1e-7 * abs(orep["E"])
+    ph = host(phi)
+    r = O.apply_H(po, ph, ph) - O.chemical_potential(po, ph) * ph
+    assert np.max(np.abs(r)) < 1.01e-8
+
+
+def test_pcg_3d_per_iterate_and_converged(G):
+    n, L = (32, 32, 32), (6.0, 6.0, 6.0)
+    V = I.harmonic(n, L, [1.0, 1.0, 2.0])
+    eta, om = 100.0, 0.5
+    po = O.Problem(n, L, eta, om, V)
+    m = I.mesh(n, L)
+    phi0 = I.perturbed(I.normalise(I.anisotropic_gaussian(n, L, [1.0, 1.0, 2.0]) * (0.5 + 0.5 * (m[0] + 1j * m[1])), n, L), 4, n, L)
+    K = 10
+    _, orep = O.pcg_solve(po, phi0, O.SolveOptions(max_iter=K), keep_iterates=(K,))
+    with make(n, L, eta, om, V, 0, G) as ctx:
+        phi = dev(phi0)
+        o = G.solve_opts_default()
+        o.max_iter = K
+        rep = ctx.pcg_solve(phi, o, log_cap=32)
+        for n_ in range(K + 1):
+            assert abs(rep["log"][n_, 2] - orep["log"][n_]["E"]) <= 1e-12 * abs(orep["log"][n_]["E"])
+        assert phase_aligned_rel_l2(host(phi), orep["iterates"][K]) < 1e-9
+        phi = dev(phi0)
+        rep = ctx.pcg_solve(phi, check=True)
+    _, oconv = O.pcg_solve(po, phi0, O.SolveOptions())
+    assert abs(rep["E"] - oconv["E"]) <= 1e-10 * abs(oconv["E"])
+
+
+def test_pcg_host_buffers_and_restart_from_solution(G):
+    w, po = _workload_problem("c64_2d")
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 0, G) as ctx:
+        phi = np.ascontiguousarray(w["phi0"].copy())
+        rep = ctx.pcg_solve(phi, check=True)
+        assert rep["res_inf"] < 1e-8
+        rep2 = ctx.pcg_solve(phi, check=True)  # resume from the converged state
+        assert rep2["iters"] == 0 and abs(rep2["E"] - rep["E"]) <= 1e-13 * abs(rep["E"])
+
+
+def test_pcg_error_statuses(G):
+    n, L = (16, 16), (4.0, 4.0)
+    V = I.harmonic(n, L)
+    with make(n, L, 10.0, 0.3, V, 0, G) as ctx:
+        phi = dev(I.phi_a(n, L))
+        o = G.solve_opts_default()
+        o.max_iter = 3
+        rep = ctx.pcg_solve(phi, o)
+        assert rep["status"] == G.GPE_ERR_NOT_CONVERGED and rep["iters"] == 3
+        bad = I.phi_a(n, L)
+        bad[3, 4] = np.nan
+        rep = ctx.pcg_solve(dev(bad))
+        assert rep["status"] == G.GPE_ERR_NONFINITE
+        # the context stays usable after a failed solve
+        rep = ctx.pcg_solve(dev(I.phi_a(n, L)), check=True)
+        assert rep["status"] == G.GPE_OK
+    Vneg = V - 1e6  # alpha + V + eta|phi|^2 < 0 somewhere: P_V undefined
+    with make(n, L, 10.0, 0.3, Vneg, 0, G) as ctx:
+        rep = ctx.pcg_solve(dev(I.phi_a(n, L)))
+        assert rep["status"] == G.GPE_ERR_PRECOND
+
+
+# ----------------------------------------------------- full-size workloads
+@pytest.mark.parametrize("name", ["fast256_2d", "rot128_3d"])
+def test_full_size_mixed_solve_verified_by_oracle(G, name):
+    """The workloads the benchmark times, in its configuration (mixed precision,
+    graph loop): the oracle evaluates the returned state's energy and residual."""
+    w, po = _workload_problem(name)
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 1, G) as ctx:
+        phi = dev(w["phi0"])
+        rep = ctx.pcg_solve(phi, check=True)
+    assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
+    ph = host(phi)
+    lam = O.chemical_potential(po, ph)
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert abs(O.energy(po, ph) - rep["E"]) <= 1e-12 * abs(rep["E"])
+    assert abs(O.norm(po, ph) - 1.0) < 1e-12
