@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the same pass kernels from a host loop instead of one graph with a device-side "
+                         "loop (for ncu launch lists: ncu cannot profile kernel nodes of graphs with conditional "
+                         "nodes)")
     return ap.parse_args()
 
 
@@ -187,9 +191,12 @@ def main():
     phi_d = torch.empty_like(phi0_d)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
+    opts = gpe.solve_opts_default()
+    opts.use_graph = 0 if args.no_graph else 1
+
     def solve_dev():
         phi_d.copy_(phi0_d)
-        return ctx.pcg_solve(phi_d, check=True)
+        return ctx.pcg_solve(phi_d, opts, check=True)
 
     for _ in range(max(args.warmup, 3)):
         rep = solve_dev()
@@ -234,7 +241,7 @@ def main():
         l2_flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.pcg_solve(phi_h.data_ptr(), check=True)
+        ctx.pcg_solve(phi_h.data_ptr(), opts, check=True)
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)

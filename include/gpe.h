@@ -75,10 +75,13 @@ typedef struct {
   int max_backtracks;   /* trial step halvings before a step is taken anyway [30] */
   int cg;               /* 1: Algorithm 2 (PCG), 0: Algorithm 1 (PG) [1] */
   /* GPE_MIXED only: the complex64 phase ends, and the complex128 phase
-   * restarts the conjugate directions, when ||r||_inf has not halved within
-   * stall_window iterations, or falls below switch_res. */
-  int stall_window;     /* [40] */
-  double switch_res;    /* [1e-6] */
+   * restarts the conjugate directions (beta = 0), when ||r||_inf falls below
+   * switch_res, or -- switch_res <= 0 -- below 4x an estimate of the
+   * single-precision floor, eps32 (max_k |k|^2/2 + max V + |lambda|) max|phi|;
+   * or when ||r||_inf has not halved within stall_window iterations while
+   * within 3x of that threshold. */
+  int stall_window;     /* [500] */
+  double switch_res;    /* [0: automatic] */
   int max_iter_lo;      /* cap on complex64-phase iterations [max_iter] */
   int use_graph;        /* 1: one CUDA graph launch with a device-side loop; 0: host loop [1] */
 } gpe_solve_opts;
@@ -112,7 +115,7 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
 
 /* Create a context for problem *prob.
  *  V      : real potential on the grid, float64, [z][y][x]; host or device;
- *           copied (the caller keeps ownership).
+ *           copied (the caller keeps ownership); must be finite.
  *  stream : cudaStream_t (NULL = legacy default stream) that orders all work.
  * Allocates all device workspace (fields, tables, reduction buffers) once.
  * Errors: GPE_ERR_ARG (null pointers, dim not 2/3, n not a power of two in

@@ -36,7 +36,6 @@ struct PrecBufs {
   void* t = nullptr;
   void* s = nullptr;
   void* r_prev = nullptr;
-  cudaGraphExec_t exec = nullptr;
 };
 
 std::string g_create_error;
@@ -60,8 +59,10 @@ struct gpe_ctx {
   double* log_dev = nullptr;
   int log_dev_cap = 0;
   PassPlan plan[3];  // per axis
+  double vmax = 0.0;  // max V on the grid
   int max_threads[2] = {512, 256};
-  bool warmed[2] = {false, false};
+  bool warmed[3] = {false, false, false};
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // per launch mode
 };
 
 #define GPE_CU(ctx, call)                                                                  \
@@ -127,8 +128,35 @@ static PassArgs base_args(gpe_ctx* c, int prec, int axis) {
   return a;
 }
 
-static cudaError_t launch(int prec, Pass pass, const PassArgs& a, cudaStream_t st) {
-  return prec ? launch_pass_f64(pass, a, st) : launch_pass_f32(pass, a, st);
+static cudaError_t launch(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
+  return launch_pass(mode, pass, a, st);
+}
+
+// Buffers of one solver iteration.  State fields (phi, H phi, r_prev, V) and
+// direction fields (P_C workspace s, p) may live in different precisions
+// (launch mode 2); tab_h / tab_d select the table precision of the H passes
+// and of the direction passes.
+struct IterBufs {
+  int mode;
+  int tab_h, tab_d;
+  void* phi;
+  void* t;
+  void* r_prev;
+  const void* V;
+  void* s;
+  void* p;
+};
+
+static IterBufs iter_bufs(gpe_ctx* c, int mode) {
+  IterBufs b;
+  b.mode = mode;
+  const int sp = mode == 0 ? 0 : 1;  // state precision
+  const int dp = mode == 1 ? 1 : 0;  // direction precision
+  b.tab_h = sp;
+  b.tab_d = dp;
+  b.phi = c->pb[sp].phi; b.t = c->pb[sp].t; b.r_prev = c->pb[sp].r_prev; b.V = c->pb[sp].V;
+  b.s = c->pb[dp].s; b.p = c->pb[dp].p;
+  return b;
 }
 
 template <typename T>
@@ -180,8 +208,9 @@ static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
 }
 
 static void free_ctx(gpe_ctx* c) {
+  for (auto& e : c->exec)
+    if (e) cudaGraphExecDestroy(e);
   for (auto& b : c->pb) {
-    if (b.exec) cudaGraphExecDestroy(b.exec);
     for (int i = 0; i < 3; ++i) { cudaFree(b.xi[i]); cudaFree(b.xc[i]); cudaFree(b.tw[i]); }
     cudaFree(b.V); cudaFree(b.phi); cudaFree(b.p); cudaFree(b.t); cudaFree(b.s); cudaFree(b.r_prev);
   }
@@ -198,8 +227,8 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->theta_default = 0.1;
   o->max_backtracks = 30;
   o->cg = 1;
-  o->stall_window = 40;
-  o->switch_res = 1e-6;
+  o->stall_window = 500;
+  o->switch_res = 0.0;
   o->max_iter_lo = 0;
   o->use_graph = 1;
   return GPE_OK;
@@ -237,6 +266,18 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
   if (cudaMalloc(&V64, 8 * (size_t)c->N) != cudaSuccess) { c->err = "cudaMalloc V"; return fail(GPE_ERR_CUDA); }
   if (cudaMemcpy(V64, V, 8 * (size_t)c->N, cudaMemcpyDefault) != cudaSuccess) {
     cudaFree(V64); c->err = "copy of V failed"; return fail(GPE_ERR_CUDA);
+  }
+  {
+    std::vector<double> Vh((size_t)c->N);
+    if (cudaMemcpy(Vh.data(), V64, 8 * (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaFree(V64); c->err = "copy of V failed"; return fail(GPE_ERR_CUDA);
+    }
+    double vm = -1e300;
+    for (double v : Vh) {
+      if (!std::isfinite(v)) { cudaFree(V64); c->err = "V must be finite"; return fail(GPE_ERR_ARG); }
+      vm = v > vm ? v : vm;
+    }
+    c->vmax = vm;
   }
   gpe_status s = alloc_prec(c, 1, V64);
   if (s == GPE_OK && prob->prec == GPE_MIXED) s = alloc_prec(c, 0, V64);
@@ -308,26 +349,27 @@ extern "C" gpe_status gpe_energy(gpe_ctx* c, const void* phi, double out[8]) {
 }
 
 // P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
-static gpe_status run_PC(gpe_ctx* c, int prec, const void* phi, const void* r, double alpha, void* out, Ctl* ctl,
-                         bool solver) {
-  PassArgs a = base_args(c, prec, 0);
-  a.ctl = ctl; a.solver = solver; a.phi = phi; a.r_in = r; a.api_alpha = alpha;
-  a.s = c->pb[prec].s; a.t = c->pb[prec].t; a.r_prev = c->pb[prec].r_prev; a.p = c->pb[prec].p; a.out = out;
-  GPE_CU(c, launch(prec, P_C1, a, c->st));
+static gpe_status run_PC(gpe_ctx* c, const IterBufs& b, const void* r, double alpha, void* out, Ctl* ctl,
+                         bool solver, cudaStream_t st) {
+  PassArgs a = base_args(c, b.tab_d, 0);
+  a.V = b.V;
+  a.ctl = ctl; a.solver = solver; a.phi = b.phi; a.r_in = r; a.api_alpha = alpha;
+  a.s = b.s; a.t = b.t; a.r_prev = b.r_prev; a.p = b.p; a.out = out;
+  GPE_CU(c, launch(b.mode, P_C1, a, st));
   if (c->dim == 3) {
-    PassArgs b = base_args(c, prec, 1);
-    b.ctl = ctl; b.solver = solver; b.s = a.s;
-    GPE_CU(c, launch(prec, P_CFWD, b, c->st));
+    PassArgs y = base_args(c, b.tab_d, 1);
+    y.ctl = ctl; y.solver = solver; y.s = b.s;
+    GPE_CU(c, launch(b.mode, P_CFWD, y, st));
   }
-  PassArgs k = base_args(c, prec, c->dim - 1);
-  k.ctl = ctl; k.solver = solver; k.s = a.s; k.api_alpha = alpha;
-  GPE_CU(c, launch(prec, P_CCORE, k, c->st));
+  PassArgs k = base_args(c, b.tab_d, c->dim - 1);
+  k.ctl = ctl; k.solver = solver; k.s = b.s; k.api_alpha = alpha;
+  GPE_CU(c, launch(b.mode, P_CCORE, k, st));
   if (c->dim == 3) {
-    PassArgs b = base_args(c, prec, 1);
-    b.ctl = ctl; b.solver = solver; b.s = a.s;
-    GPE_CU(c, launch(prec, P_CINV, b, c->st));
+    PassArgs y = base_args(c, b.tab_d, 1);
+    y.ctl = ctl; y.solver = solver; y.s = b.s;
+    GPE_CU(c, launch(b.mode, P_CINV, y, st));
   }
-  GPE_CU(c, launch(prec, P_C3, a, c->st));
+  GPE_CU(c, launch(b.mode, P_C3, a, st));
   return GPE_OK;
 }
 
@@ -340,49 +382,44 @@ extern "C" gpe_status gpe_precond(gpe_ctx* c, const void* phi, const void* r, do
     gpe_status s = run_H(c, prec, phi, phi, c->pb[prec].t, c->ctl_api);  // lambda~ into ctl_api->alpha
     if (s != GPE_OK) return s;
   }
-  return run_PC(c, prec, phi, r, alpha, out, c->ctl_api, false);
+  IterBufs b = iter_bufs(c, prec);
+  b.phi = const_cast<void*>(phi);
+  return run_PC(c, b, r, alpha, out, c->ctl_api, false, c->st);
 }
 
-// One PCG iteration (all passes) in precision prec, on the solver buffers.
-static gpe_status enqueue_iteration(gpe_ctx* c, int prec, cudaStream_t st, unsigned long long cond) {
-  PrecBufs& b = c->pb[prec];
+// One PCG iteration (all passes) in launch mode `mode`, on the solver buffers.
+static gpe_status enqueue_iteration(gpe_ctx* c, int mode, cudaStream_t st, unsigned long long cond) {
+  const IterBufs b = iter_bufs(c, mode);
   Ctl* ctl = c->ctl_solve;
-  cudaStream_t keep = c->st;
-  c->st = st;
-  gpe_status s = GPE_OK;
-  do {
-    // H phi (with the retraction phi_{n+1} = (c phi_n + s p_n/|p_n|)/nrm folded into the x pass)
-    PassArgs a = base_args(c, prec, 0);
-    a.ctl = ctl; a.solver = 1; a.phi = b.phi; a.phi_out = b.phi; a.p = b.p; a.t = b.t;
-    if (launch(prec, P_HX, a, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
-    for (int ax = 1; ax < c->dim && s == GPE_OK; ++ax) {
-      PassArgs h = base_args(c, prec, ax);
-      h.ctl = ctl; h.solver = 1; h.phi = b.phi; h.t = b.t; h.last_axis = (ax == c->dim - 1);
-      if (launch(prec, P_HMID, h, st) != cudaSuccess) s = GPE_ERR_CUDA;
-    }
-    if (s != GPE_OK) break;
-    // P_C r_n
-    s = run_PC(c, prec, b.phi, nullptr, 0.0, nullptr, ctl, true);
-    if (s != GPE_OK) break;
-    // p_n and the step-size moments
-    PassArgs x = base_args(c, prec, 0);
-    x.ctl = ctl; x.solver = 1; x.phi = b.phi; x.s = b.s; x.t = b.t; x.p = b.p;
-    if (launch(prec, P_AX, x, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
-    for (int ax = 1; ax < c->dim; ++ax) {
-      PassArgs m = base_args(c, prec, ax);
-      m.ctl = ctl; m.solver = 1; m.phi = b.phi; m.p = b.p; m.last_axis = (ax == c->dim - 1);
-      m.cond = m.last_axis ? cond : 0ull;
-      if (launch(prec, P_AMID, m, st) != cudaSuccess) { s = GPE_ERR_CUDA; break; }
-    }
-  } while (0);
-  c->st = keep;
-  if (s != GPE_OK) c->err = std::string("pass launch failed: ") + cudaGetErrorString(cudaGetLastError());
-  return s;
+  // H phi (with the retraction phi_{n+1} = (c phi_n + s p_n/|p_n|)/nrm folded into the x pass)
+  PassArgs a = base_args(c, b.tab_h, 0);
+  a.V = b.V;
+  a.ctl = ctl; a.solver = 1; a.phi = b.phi; a.phi_out = b.phi; a.p = b.p; a.t = b.t;
+  GPE_CU(c, launch(mode, P_HX, a, st));
+  for (int ax = 1; ax < c->dim; ++ax) {
+    PassArgs h = base_args(c, b.tab_h, ax);
+    h.ctl = ctl; h.solver = 1; h.phi = b.phi; h.t = b.t; h.last_axis = (ax == c->dim - 1);
+    GPE_CU(c, launch(mode, P_HMID, h, st));
+  }
+  // P_C r_n
+  gpe_status s = run_PC(c, b, nullptr, 0.0, nullptr, ctl, true, st);
+  if (s != GPE_OK) return s;
+  // p_n and the step-size moments
+  PassArgs x = base_args(c, b.tab_d, 0);
+  x.V = b.V;
+  x.ctl = ctl; x.solver = 1; x.phi = b.phi; x.s = b.s; x.t = b.t; x.p = b.p;
+  GPE_CU(c, launch(mode, P_AX, x, st));
+  for (int ax = 1; ax < c->dim; ++ax) {
+    PassArgs m = base_args(c, b.tab_d, ax);
+    m.ctl = ctl; m.solver = 1; m.phi = b.phi; m.p = b.p; m.last_axis = (ax == c->dim - 1);
+    m.cond = m.last_axis ? cond : 0ull;
+    GPE_CU(c, launch(mode, P_AMID, m, st));
+  }
+  return GPE_OK;
 }
 
-static gpe_status build_graph(gpe_ctx* c, int prec) {
-  PrecBufs& b = c->pb[prec];
-  if (b.exec) return GPE_OK;
+static gpe_status build_graph(gpe_ctx* c, int mode) {
+  if (c->exec[mode]) return GPE_OK;
   cudaGraph_t g = nullptr;
   GPE_CU(c, cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
@@ -395,49 +432,50 @@ static gpe_status build_graph(gpe_ctx* c, int prec) {
   GPE_CU(c, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
   GPE_CU(c, cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  gpe_status s = enqueue_iteration(c, prec, c->cap, (unsigned long long)h);
+  gpe_status s = enqueue_iteration(c, mode, c->cap, (unsigned long long)h);
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap, &captured);
   if (s != GPE_OK) { cudaGraphDestroy(g); return s; }
   if (e != cudaSuccess) { c->err = std::string("capture: ") + cudaGetErrorString(e); cudaGraphDestroy(g); return GPE_ERR_CUDA; }
-  e = cudaGraphInstantiate(&b.exec, g, 0);
+  e = cudaGraphInstantiate(&c->exec[mode], g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) { c->err = std::string("instantiate: ") + cudaGetErrorString(e); b.exec = nullptr; return GPE_ERR_CUDA; }
+  if (e != cudaSuccess) { c->err = std::string("instantiate: ") + cudaGetErrorString(e); c->exec[mode] = nullptr; return GPE_ERR_CUDA; }
   return GPE_OK;
 }
 
 // Make sure every pass kernel of precision prec has had its attributes set
 // (first launch) before capture: one iteration with done = 1 exits at once.
-static gpe_status warm_kernels(gpe_ctx* c, int prec) {
-  if (c->warmed[prec]) return GPE_OK;
+static gpe_status warm_kernels(gpe_ctx* c, int mode) {
+  if (c->warmed[mode]) return GPE_OK;
   Ctl h;
   std::memset(&h, 0, sizeof(h));
   h.done = 1;
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
-  gpe_status s = enqueue_iteration(c, prec, c->st, 0ull);
+  gpe_status s = enqueue_iteration(c, mode, c->st, 0ull);
   if (s != GPE_OK) return s;
   GPE_CU(c, cudaStreamSynchronize(c->st));
-  c->warmed[prec] = true;
+  c->warmed[mode] = true;
   return GPE_OK;
 }
 
-static gpe_status run_phase(gpe_ctx* c, int prec, Ctl& h, const gpe_solve_opts& o) {
-  PrecBufs& b = c->pb[prec];
-  const size_t bytes = (prec ? 16 : 8) * (size_t)c->N;
-  gpe_status s = warm_kernels(c, prec);
+static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& o) {
+  const IterBufs b = iter_bufs(c, mode);
+  const size_t sbytes = (b.tab_h ? 16 : 8) * (size_t)c->N;
+  const size_t dbytes = (b.tab_d ? 16 : 8) * (size_t)c->N;
+  gpe_status s = warm_kernels(c, mode);
   if (s != GPE_OK) return s;
-  GPE_CU(c, cudaMemsetAsync(b.p, 0, bytes, c->st));
-  GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, bytes, c->st));
+  GPE_CU(c, cudaMemsetAsync(b.p, 0, dbytes, c->st));
+  GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, sbytes, c->st));
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
-  GPE_CU(c, launch_init_norm(prec, b.phi, c->N, c->weight, c->ctl_solve, c->st));
+  GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->st));
   if (o.use_graph) {
-    s = build_graph(c, prec);
+    s = build_graph(c, mode);
     if (s != GPE_OK) return s;
-    GPE_CU(c, cudaGraphLaunch(b.exec, c->st));
+    GPE_CU(c, cudaGraphLaunch(c->exec[mode], c->st));
   } else {
     int k = 0;
     while (true) {
-      s = enqueue_iteration(c, prec, c->st, 0ull);
+      s = enqueue_iteration(c, mode, c->st, 0ull);
       if (s != GPE_OK) return s;
       if (++k % 16 == 0) {
         int done = 0;
@@ -481,6 +519,15 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
   h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
   h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
   h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
+  {
+    double k2 = 0.0;  // max over the grid of |k|^2 / 2 (corner mode -M/2 on every axis)
+    for (int i = 0; i < c->dim; ++i) {
+      const double km = 0.5 * c->n[i] * M_PI / c->prob.L[i];
+      k2 += 0.5 * km * km;
+    }
+    h.floor_coef = 5.96e-8 * (k2 + (c->vmax > 0.0 ? c->vmax : 0.0));
+    h.switch_fac = 4.0;
+  }
 
   int iters_lo = 0;
   gpe_status s;
@@ -499,7 +546,7 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
     if (go_on && h.iter < o.max_iter) {
       h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = 1; h.stop_dE = 0;
       h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter;
-      s = run_phase(c, 1, h, o);
+      s = run_phase(c, 2, h, o);  // refinement: FP64 state, FP32 direction
       if (s != GPE_OK) return s;
     }
   } else {

@@ -40,6 +40,9 @@ struct Ctl {
   double dE;
   double anchor_res; int anchor_iter;   // stall detection (mixed phase)
   int pad0;
+  double phimax;      // max |phi_n| (H x pass)
+  double floor_coef;  // eps32 (max 1/2|k|^2 + max V): complex64 residual floor per unit |phi|
+  double switch_fac;  // complex64 phase ends when ||r||_inf < switch_fac * floor estimate
   // ---- raw sums written by pass finalisers ----
   double hsum[3][kMaxMoments];  // H passes, per axis
   double psum[kMaxMoments];     // P_C passes
@@ -100,10 +103,10 @@ struct PassArgs {
   unsigned long long cond;  // cudaGraphConditionalHandle (0 = none)
 };
 
-// Launch one pass in precision T (float or double).  Returns cudaSuccess or
-// the launch error.  Defined in gpe_kernels_f32.cu / gpe_kernels_f64.cu.
-cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st);
-cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st);
+// Launch one pass.  mode 0: complex64; 1: complex128; 2: refinement split
+// (FP64 phi, H phi, r and V; FP32 P_C workspace and direction p; the x pass
+// of H phi reads p in FP32).  Returns cudaSuccess or the launch error.
+cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st);
 
 // Per-group launchers (gpe_k_<prec>_<group>.cu).
 cudaError_t launch_group_f32_h(Pass pass, const PassArgs& a, cudaStream_t st);
@@ -112,6 +115,7 @@ cudaError_t launch_group_f32_a(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_h(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_c(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_a(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_split(Pass pass, const PassArgs& a, cudaStream_t st);
 
 // Small elementwise/control kernels (gpe_misc.cu).
 cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st);

@@ -1,10 +1,10 @@
-// Instantiations of the pass kernels: precision float, group 'a' (split for parallel compilation).
+// Instantiations of the pass kernels: float transforms, group 'a' (split for parallel compilation).
 #include "gpe_passes.cuh"
 namespace gpe {
 cudaError_t launch_group_f32_a(Pass pass, const PassArgs& a, cudaStream_t st) {
   switch (pass) {
-    case P_AX: return launch_role<float, P_AX>(a, st);
-    case P_AMID: return launch_role<float, P_AMID>(a, st);
+    case P_AX: return launch_role<0, P_AX>(a, st);
+    case P_AMID: return launch_role<0, P_AMID>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

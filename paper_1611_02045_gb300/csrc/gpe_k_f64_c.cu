@@ -1,13 +1,13 @@
-// Instantiations of the pass kernels: precision double, group 'c' (split for parallel compilation).
+// Instantiations of the pass kernels: double transforms, group 'c' (split for parallel compilation).
 #include "gpe_passes.cuh"
 namespace gpe {
 cudaError_t launch_group_f64_c(Pass pass, const PassArgs& a, cudaStream_t st) {
   switch (pass) {
-    case P_C1: return launch_role<double, P_C1>(a, st);
-    case P_CFWD: return launch_role<double, P_CFWD>(a, st);
-    case P_CCORE: return launch_role<double, P_CCORE>(a, st);
-    case P_CINV: return launch_role<double, P_CINV>(a, st);
-    case P_C3: return launch_role<double, P_C3>(a, st);
+    case P_C1: return launch_role<1, P_C1>(a, st);
+    case P_CFWD: return launch_role<1, P_CFWD>(a, st);
+    case P_CCORE: return launch_role<1, P_CCORE>(a, st);
+    case P_CINV: return launch_role<1, P_CINV>(a, st);
+    case P_C3: return launch_role<1, P_C3>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -4,7 +4,7 @@
 
 namespace gpe {
 
-cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st) {
+static cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st) {
   switch (pass) {
     case P_HX: case P_HMID: return launch_group_f32_h(pass, a, st);
     case P_AX: case P_AMID: return launch_group_f32_a(pass, a, st);
@@ -12,11 +12,24 @@ cudaError_t launch_pass_f32(Pass pass, const PassArgs& a, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st) {
+static cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st) {
   switch (pass) {
     case P_HX: case P_HMID: return launch_group_f64_h(pass, a, st);
     case P_AX: case P_AMID: return launch_group_f64_a(pass, a, st);
     default: return launch_group_f64_c(pass, a, st);
+  }
+}
+
+cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
+  if (mode == 0) return launch_pass_f32(pass, a, st);
+  if (mode == 1) return launch_pass_f64(pass, a, st);
+  // refinement split: H phi in FP64 (y/z passes are plain complex128), the
+  // contiguous direction passes mix precisions, the strided direction passes
+  // are plain complex64.
+  switch (pass) {
+    case P_HX: case P_C1: case P_C3: case P_AX: return launch_group_split(pass, a, st);
+    case P_HMID: return launch_pass_f64(pass, a, st);
+    default: return launch_pass_f32(pass, a, st);
   }
 }
 

@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "gpe_fft.cuh"
 #include "gpe_internal.h"
 
@@ -91,10 +93,13 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const PassArgs& a, d
   double w[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) w[k] = 0.0;  // all slots hold non-negative values or sums
+  // L2-coherent loads (__ldcg), unrolled so that several blocks' partials are
+  // in flight at once; the summation order stays fixed.
+#pragma unroll 4
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const volatile double* pb = a.partials + (size_t)b * kMaxMoments;
+    const double* pb = a.partials + (size_t)b * kMaxMoments;
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = red_op<K, MAXMASK>(w[k], pb[k], k);
+    for (int k = 0; k < K; ++k) w[k] = red_op<K, MAXMASK>(w[k], __ldcg(pb + k), k);
   }
   block_reduce<K, MAXMASK>(w, red_sm);
   if (threadIdx.x == 0) {
@@ -123,6 +128,7 @@ static __device__ void finalize_H(const PassArgs& a) {
   c->pot = w * c->hsum[0][2];
   c->U0 = w * c->hsum[0][3];
   c->norm2 = w * c->hsum[0][4];
+  c->phimax = sqrt(c->hsum[0][5]);
   const double quad = c->kin + c->rot + c->pot;
   c->lam = quad + a.eta * c->U0;                           // <phi, H phi>
   c->alpha = c->kin + c->pot + a.eta * c->U0;              // lambda~ (no rotation term)
@@ -156,8 +162,13 @@ static __device__ void finalize_C1(const PassArgs& a, const double (&tot)[3]) {
   } else if (c->iter >= c->max_iter) {
     c->status = ST_NOT_CONVERGED; c->done = 1;
   } else if (c->lo_phase) {
+    // complex64 phase: stop at the single-precision residual floor, estimated
+    // as eps32 (max |k|^2/2 + max V + |lambda|) max|phi|, or on a stall near it
+    const double floor_est = (c->floor_coef + 5.96e-8 * fabs(c->lam)) * c->phimax;
+    const double thr = c->switch_res > 0.0 ? c->switch_res : c->switch_fac * floor_est;
     if (c->res_inf <= 0.5 * c->anchor_res) { c->anchor_res = c->res_inf; c->anchor_iter = c->iter; }
-    if (c->res_inf < c->switch_res || c->iter - c->anchor_iter >= c->stall_window || nphase >= c->max_iter_phase) {
+    const bool stalled = c->iter - c->anchor_iter >= c->stall_window && c->res_inf < 3.0 * thr;
+    if (c->res_inf < thr || stalled || nphase >= c->max_iter_phase) {
       c->switch_req = 1; c->status = ST_NOT_CONVERGED; c->done = 1;
     }
   }
@@ -252,17 +263,28 @@ __device__ __forceinline__ const T* tab(const void* p) { return static_cast<cons
 
 // ---------------------------------------------------------------------------
 // Contiguous (x) passes.  Block = lpb lines x Tl threads; tid = t + Tl*l.
+//
+// Three element types: TF for the line transform, TS for the state fields
+// (phi, H phi, r_{n-1}, V) and TD for the direction fields (P_C workspace s,
+// P r, p).  TF = TS = TD gives the plain complex64 or complex128 passes; the
+// refinement passes use TS = double with TF = TD = float for the direction
+// (P_C r and the moments of A p), and TF = TS = double, TD = float for H phi.
 // ---------------------------------------------------------------------------
-// Max threads per block: 512 in single precision, 256 in double (register budget).
+// Max threads per block: 512 with single-precision transforms, 256 with double.
 template <typename T> struct MaxThreads { static constexpr int value = sizeof(T) == 8 ? 256 : 512; };
 
-template <typename T, int M, int ROLE>
-__global__ void __launch_bounds__(MaxThreads<T>::value) pass_x(PassArgs a) {
-  using C = cplx<T>;
+template <typename To, typename From>
+__device__ __forceinline__ cplx<To> cconv(From v) { return cmk<cplx<To>>((To)v.x, (To)v.y); }
+
+template <typename TF, typename TS, typename TD, int M, int ROLE>
+__global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
+  using CF = cplx<TF>;
+  using CS = cplx<TS>;
+  using CD = cplx<TD>;
   constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
   constexpr int LS = M + M / 16;  // padded line stride in shared memory
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
+  CF* sm = reinterpret_cast<CF*>(smraw);
   Ctl* ctl = a.ctl;
   if (a.solver && ctl->done) return;
 
@@ -270,93 +292,94 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_x(PassArgs a) {
   const long long line = (long long)blockIdx.x * a.lpb + l;
   const long long base = line * M;
   const int iy = (int)(line % a.ny);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
-  const T* __restrict__ xi = tab<T>(a.xi[0]);
-  const T* __restrict__ V = tab<T>(a.V);
+  const CF* __restrict__ tw = static_cast<const CF*>(a.tw);
+  const TF* __restrict__ xi = tab<TF>(a.xi[0]);
+  const TS* __restrict__ V = tab<TS>(a.V);
   auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
-  const T invM = T(1) / T(M);
+  const TF invM = TF(1) / TF(M);
 
-  C v[E];
+  CF v[E];
   if constexpr (ROLE == P_HX) {
-    // ---- H_phi f, x part, plus the real-space terms --------------------------------
-    const C* __restrict__ phi = static_cast<const C*>(a.phi);
-    const C* __restrict__ f = static_cast<const C*>(a.f ? a.f : a.phi);
-    C ph[E];
-    T vv[E];
+    // ---- H_phi f, x part, plus the real-space terms (TF == TS) --------------------
+    static_assert(sizeof(TF) == sizeof(TS), "H passes transform the state precision");
+    const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
+    const CS* __restrict__ f = static_cast<const CS*>(a.f ? a.f : a.phi);
+    CS ph[E];
     const bool retract = a.solver && ctl->retract;
-    const T cc = T(retract ? ctl->c * ctl->inv_nrm : 1.0);
-    const T ss = T(retract ? ctl->s * ctl->inv_np * ctl->inv_nrm : 0.0);
-    const C* __restrict__ p = static_cast<const C*>(a.p);
-    C* __restrict__ phi_out = static_cast<C*>(a.phi_out);
+    const TS cc = TS(retract ? ctl->c * ctl->inv_nrm : 1.0);
+    const TS ss = TS(retract ? ctl->s * ctl->inv_np * ctl->inv_nrm : 0.0);
+    const CD* __restrict__ p = static_cast<const CD*>(a.p);
+    CS* __restrict__ phi_out = static_cast<CS*>(a.phi_out);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      vv[q] = V[g];
-      C x = phi[g];
+      CS x = phi[g];
       if (retract) {
-        const C pq = p[g];
-        x = cmk<C>(cc * x.x + ss * pq.x, cc * x.y + ss * pq.y);
+        const CS pq = cconv<TS>(p[g]);
+        x = cmk<CS>(cc * x.x + ss * pq.x, cc * x.y + ss * pq.y);
         phi_out[g] = x;
       }
       ph[q] = x;
-      v[q] = (a.f && !a.solver) ? f[g] : x;
+      v[q] = cconv<TF>((a.f && !a.solver) ? f[g] : x);
     }
     line_dft<M, E, -1>(v, sm, si, t, tw);
-    const T y = tab<T>(a.xc[1])[iy];
-    const T om = T(a.omega);
-    T akin = 0, arot = 0;
+    const TF y = tab<TF>(a.xc[1])[iy];
+    const TF om = TF(a.omega);
+    TF akin = 0, arot = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      const T k = xi[t + q * Tl];
-      const T mk = T(0.5) * k * k, mr = om * y * k;
-      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+      const TF k = xi[t + q * Tl];
+      const TF mk = TF(0.5) * k * k, mr = om * y * k;
+      const TF a2 = v[q].x * v[q].x + v[q].y * v[q].y;
       akin += mk * a2; arot += mr * a2;
       v[q] = cscale(v[q], (mk + mr) * invM);
     }
     line_dft<M, E, +1>(v, sm, si, t, tw);
-    C* __restrict__ tout = static_cast<C*>(a.t);
-    const T eta = T(a.eta);
-    T apot = 0, au2 = 0, an2 = 0;
+    CS* __restrict__ tout = static_cast<CS*>(a.t);
+    const TS eta = TS(a.eta);
+    TS apot = 0, au2 = 0, an2 = 0, umax = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const T u = ph[q].x * ph[q].x + ph[q].y * ph[q].y;
-      const T m = vv[q] + eta * u;
-      const C fq = (a.f && !a.solver) ? f[g] : ph[q];  // the operand f (re-read in API mode)
-      tout[g] = cmk<C>(v[q].x + m * fq.x, v[q].y + m * fq.y);
-      apot += vv[q] * u; au2 += u * u; an2 += u;
+      const TS vv = V[g];
+      const TS u = ph[q].x * ph[q].x + ph[q].y * ph[q].y;
+      const TS m = vv + eta * u;
+      const CS fq = (a.f && !a.solver) ? f[g] : ph[q];  // the operand f (re-read in API mode)
+      tout[g] = cmk<CS>(TS(v[q].x) + m * fq.x, TS(v[q].y) + m * fq.y);
+      apot += vv * u; au2 += u * u; an2 += u; umax = fmax(umax, u);
     }
-    double acc[5] = {double(akin) * double(invM), double(arot) * double(invM), double(apot), double(au2), double(an2)};
-    double tot[5];
-    if (grid_reduce<5, 0u>(acc, a, tot) && threadIdx.x == 0) {
+    double acc[6] = {double(akin) * double(invM), double(arot) * double(invM), double(apot), double(au2), double(an2),
+                     double(umax)};
+    double tot[6];
+    if (grid_reduce<6, 32u>(acc, a, tot) && threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < 5; ++k) ctl->hsum[0][k] = tot[k];
+      for (int k = 0; k < 6; ++k) ctl->hsum[0][k] = tot[k];
     }
   } else if constexpr (ROLE == P_C1) {
     // ---- s = FFT_x[P_V^{1/2} r], r = H phi - lambda phi (solver) or r_in (API) ----
-    const C* __restrict__ phi = static_cast<const C*>(a.phi);
-    const C* __restrict__ rin = static_cast<const C*>(a.solver ? a.t : a.r_in);
-    const T lam = T(a.solver ? ctl->lam : 0.0);
+    const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
+    const CS* __restrict__ rin = static_cast<const CS*>(a.solver ? a.t : a.r_in);
+    const TS lam = TS(a.solver ? ctl->lam : 0.0);
     const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
-    const T alpha = T(alpha_d);
-    const T eta = T(a.eta);
-    T rmax = 0, r2 = 0, bad = 0;
+    const TS alpha = TS(alpha_d);
+    const TS eta = TS(a.eta);
+    TS rmax = 0, r2 = 0, bad = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const C ph = phi[g];
-      C r = rin[g];
-      if (a.solver) r = cmk<C>(r.x - lam * ph.x, r.y - lam * ph.y);
-      const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
-      bad += (den > T(0)) ? T(0) : T(1);
-      const T a2 = r.x * r.x + r.y * r.y;
+      const CS ph = phi[g];
+      CS r = rin[g];
+      if (a.solver) r = cmk<CS>(r.x - lam * ph.x, r.y - lam * ph.y);
+      const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+      bad += (den > TS(0)) ? TS(0) : TS(1);
+      const TS a2 = r.x * r.x + r.y * r.y;
       rmax = fmax(rmax, a2); r2 += a2;
-      v[q] = cscale(r, T(1) / sqrt(den));
+      v[q] = cconv<TF>(cscale(r, TS(1) / sqrt(den)));
     }
     line_dft<M, E, -1>(v, sm, si, t, tw);
-    C* __restrict__ sout = static_cast<C*>(a.s);
+    CD* __restrict__ sout = static_cast<CD*>(a.s);
 #pragma unroll
-    for (int q = 0; q < E; ++q) sout[base + t + q * Tl] = v[q];
+    for (int q = 0; q < E; ++q) sout[base + t + q * Tl] = cconv<TD>(v[q]);
     if (a.solver) {
       double acc[3] = {double(rmax), double(r2), double(bad)};
       double tot[3];
@@ -364,41 +387,42 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_x(PassArgs a) {
     }
   } else if constexpr (ROLE == P_C3) {
     // ---- Pr = P_V^{1/2} IFFT_x[s] (the 1/N is applied in the core pass) ----
-    const C* __restrict__ phi = static_cast<const C*>(a.phi);
-    C* __restrict__ sbuf = static_cast<C*>(a.s);
+    const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
+    CD* __restrict__ sbuf = static_cast<CD*>(a.s);
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = sbuf[base + t + q * Tl];
+    for (int q = 0; q < E; ++q) v[q] = cconv<TF>(sbuf[base + t + q * Tl]);
     line_dft<M, E, +1>(v, sm, si, t, tw);
     const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
-    const T alpha = T(alpha_d);
-    const T eta = T(a.eta);
+    const TS alpha = TS(alpha_d);
+    const TS eta = TS(a.eta);
     if (!a.solver) {
-      C* __restrict__ out = static_cast<C*>(a.out);
+      CD* __restrict__ out = static_cast<CD*>(a.out);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const long long g = base + t + q * Tl;
-        const C ph = phi[g];
-        const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
-        out[g] = cscale(v[q], T(1) / sqrt(den));
+        const CS ph = phi[g];
+        const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+        out[g] = cconv<TD>(cscale(cconv<TS>(v[q]), TS(1) / sqrt(den)));
       }
       return;
     }
-    const C* __restrict__ Hphi = static_cast<const C*>(a.t);
-    C* __restrict__ rprev = static_cast<C*>(a.r_prev);
-    const C* __restrict__ pprev = static_cast<const C*>(a.p);
-    const T lam = T(ctl->lam);
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    const CS* __restrict__ Hphi = static_cast<const CS*>(a.t);
+    CS* __restrict__ rprev = static_cast<CS*>(a.r_prev);
+    const CD* __restrict__ pprev = static_cast<const CD*>(a.p);
+    const TS lam = TS(ctl->lam);
+    TS a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const C ph = phi[g];
-      const T den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
-      const C Pr = cscale(v[q], T(1) / sqrt(den));
-      sbuf[g] = Pr;
-      const C h = Hphi[g];
-      const C r = cmk<C>(h.x - lam * ph.x, h.y - lam * ph.y);
-      const C ro = rprev[g];
-      const C pp = pprev[g];
+      const CS ph = phi[g];
+      const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+      const CD Prd = cconv<TD>(cscale(cconv<TS>(v[q]), TS(1) / sqrt(den)));
+      sbuf[g] = Prd;
+      const CS Pr = cconv<TS>(Prd);  // the stored direction, as later passes see it
+      const CS h = Hphi[g];
+      const CS r = cmk<CS>(h.x - lam * ph.x, h.y - lam * ph.y);
+      const CS ro = rprev[g];
+      const CS pp = cconv<TS>(pprev[g]);
       a0 += r.x * Pr.x + r.y * Pr.y;
       a1 += (r.x - ro.x) * Pr.x + (r.y - ro.y) * Pr.y;
       a2 += Pr.x * ph.x + Pr.y * ph.y;
@@ -412,34 +436,36 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_x(PassArgs a) {
     if (grid_reduce<6, 0u>(acc, a, tot) && threadIdx.x == 0) finalize_C3(a, tot);
   } else if constexpr (ROLE == P_AX) {
     // ---- p = -Pr + beta p_prev - gamma phi ; moments for the step size ----
-    const C* __restrict__ phi = static_cast<const C*>(a.phi);
-    const C* __restrict__ Pr = static_cast<const C*>(a.s);
-    const C* __restrict__ Hphi = static_cast<const C*>(a.t);
-    C* __restrict__ pbuf = static_cast<C*>(a.p);
-    const T beta = T(ctl->beta), gamma = T(ctl->gamma);
-    T aR = 0, aV = 0, aW1 = 0, aUV = 0, aV2 = 0, aUW = 0, aVW = 0, aW2 = 0, aRho = 0;
+    const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
+    const CD* __restrict__ Pr = static_cast<const CD*>(a.s);
+    const CS* __restrict__ Hphi = static_cast<const CS*>(a.t);
+    CD* __restrict__ pbuf = static_cast<CD*>(a.p);
+    const TS beta = TS(ctl->beta), gamma = TS(ctl->gamma);
+    TS aR = 0, aV = 0, aW1 = 0, aUV = 0, aV2 = 0, aUW = 0, aVW = 0, aW2 = 0, aRho = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const C ph = phi[g], pr = Pr[g], pp = pbuf[g], h = Hphi[g];
-      const C pn = cmk<C>(-pr.x + beta * pp.x - gamma * ph.x, -pr.y + beta * pp.y - gamma * ph.y);
-      pbuf[g] = pn;
-      v[q] = pn;
-      const T u = ph.x * ph.x + ph.y * ph.y;
-      const T vr = ph.x * pn.x + ph.y * pn.y;
-      const T wq = pn.x * pn.x + pn.y * pn.y;
+      const CS ph = phi[g], h = Hphi[g];
+      const CS pr = cconv<TS>(Pr[g]), pp = cconv<TS>(pbuf[g]);
+      const CD pnd = cconv<TD>(cmk<CS>(-pr.x + beta * pp.x - gamma * ph.x, -pr.y + beta * pp.y - gamma * ph.y));
+      pbuf[g] = pnd;
+      const CS pn = cconv<TS>(pnd);  // moments of the stored p
+      v[q] = cconv<TF>(pnd);
+      const TS u = ph.x * ph.x + ph.y * ph.y;
+      const TS vr = ph.x * pn.x + ph.y * pn.y;
+      const TS wq = pn.x * pn.x + pn.y * pn.y;
       aR += h.x * pn.x + h.y * pn.y;
       aV += V[g] * wq;
       aW1 += wq; aUV += u * vr; aV2 += vr * vr; aUW += u * wq; aVW += vr * wq; aW2 += wq * wq; aRho += vr;
     }
     line_dft<M, E, -1>(v, sm, si, t, tw);
-    const T y = tab<T>(a.xc[1])[iy];
-    const T om = T(a.omega);
-    T akr = 0;
+    const TF y = tab<TF>(a.xc[1])[iy];
+    const TF om = TF(a.omega);
+    TF akr = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      const T k = xi[t + q * Tl];
-      akr += (T(0.5) * k * k + om * y * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
+      const TF k = xi[t + q * Tl];
+      akr += (TF(0.5) * k * k + om * y * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
     }
     double acc[9] = {double(aR), double(aV) + double(akr) * double(invM), double(aW1), double(aUV), double(aV2),
                      double(aUW), double(aVW), double(aW2), double(aRho)};
@@ -571,9 +597,24 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
 // ---------------------------------------------------------------------------
 // Host-side dispatch over M
 // ---------------------------------------------------------------------------
-template <typename T, int M, int ROLE>
+// Precision modes of a launch: 0 complex64, 1 complex128, 2 refinement split
+// (state in FP64, direction in FP32; H passes transform in FP64).
+template <int MODE, int ROLE> struct ModeTypes;
+template <int ROLE> struct ModeTypes<0, ROLE> { using TF = float; using TS = float; using TD = float; };
+template <int ROLE> struct ModeTypes<1, ROLE> { using TF = double; using TS = double; using TD = double; };
+template <int ROLE> struct ModeTypes<2, ROLE> {
+  static constexpr bool h = (ROLE == P_HX || ROLE == P_HMID);
+  static constexpr bool state = (ROLE == P_C1 || ROLE == P_C3 || ROLE == P_AX);
+  using TF = typename std::conditional<h, double, float>::type;
+  using TS = typename std::conditional<h || state, double, float>::type;
+  using TD = float;
+};
+
+template <int MODE, int M, int ROLE>
 cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
-  using C = cplx<T>;
+  using MT = ModeTypes<MODE, ROLE>;
+  using TF = typename MT::TF;
+  using C = cplx<TF>;
   constexpr int Tl = LineCfg<M>::Tl;
   constexpr bool contig = (ROLE == P_HX || ROLE == P_C1 || ROLE == P_C3 || ROLE == P_AX);
   int threads, smem;
@@ -585,8 +626,8 @@ cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
     smem = M * a.tx * (int)sizeof(C);
   }
   void (*kern)(PassArgs);
-  if constexpr (contig) kern = pass_x<T, M, ROLE>;
-  else kern = pass_s<T, M, ROLE>;
+  if constexpr (contig) kern = pass_x<TF, typename MT::TS, typename MT::TD, M, ROLE>;
+  else kern = pass_s<TF, M, ROLE>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -597,16 +638,16 @@ cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int ROLE>
+template <int MODE, int ROLE>
 cudaError_t launch_role(const PassArgs& a, cudaStream_t st) {
   switch (a.M) {
-    case 8: return launch_one<T, 8, ROLE>(a, st);
-    case 16: return launch_one<T, 16, ROLE>(a, st);
-    case 32: return launch_one<T, 32, ROLE>(a, st);
-    case 64: return launch_one<T, 64, ROLE>(a, st);
-    case 128: return launch_one<T, 128, ROLE>(a, st);
-    case 256: return launch_one<T, 256, ROLE>(a, st);
-    case 512: return launch_one<T, 512, ROLE>(a, st);
+    case 8: return launch_one<MODE, 8, ROLE>(a, st);
+    case 16: return launch_one<MODE, 16, ROLE>(a, st);
+    case 32: return launch_one<MODE, 32, ROLE>(a, st);
+    case 64: return launch_one<MODE, 64, ROLE>(a, st);
+    case 128: return launch_one<MODE, 128, ROLE>(a, st);
+    case 256: return launch_one<MODE, 256, ROLE>(a, st);
+    case 512: return launch_one<MODE, 512, ROLE>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,104 @@
+"""Operator microbenchmark: times one libgpe entry point on a synthetic field.
+
+    python -m paper_1611_02045_gb300.opbench --grid 256 256 512 --prec mixed --op apply_H --iters 20
+
+Prints one JSON line: median CUDA-event time per call, points, and the
+effective bandwidth for the given algorithmic bytes per point.  Also used as
+the small, self-contained program for ncu captures of single passes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, nargs="+", default=[256, 256, 512])
+    ap.add_argument("--L", type=float, default=8.0)
+    ap.add_argument("--prec", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--op", choices=["apply_H", "precond", "energy", "solve"], default="apply_H")
+    ap.add_argument("--workload", default="fast256_2d", help="for --op solve")
+    ap.add_argument("--max-iter", type=int, default=50, help="for --op solve")
+    ap.add_argument("--switch-res", type=float, default=0.0, help="for --op solve (mixed)")
+    ap.add_argument("--no-graph", action="store_true", help="for --op solve: host-driven loop")
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args()
+
+    import torch
+
+    from paper_1611_02045_gb300 import build, gpe, inputs as I
+    build.build()
+    dev = torch.device("cuda", 0)
+    prec = gpe.GPE_FP64 if a.prec == "fp64" else gpe.GPE_MIXED
+    stream = torch.cuda.current_stream()
+
+    if a.op == "solve":
+        w = I.workload(a.workload)
+        ctx = gpe.Context(w["n"], w["L"], w["eta"], w["omega"], w["V"], prec=prec)
+        phi0 = torch.from_numpy(w["phi0"].copy()).to(dev)
+        phi = torch.empty_like(phi0)
+        opts = gpe.solve_opts_default()
+        opts.max_iter = a.max_iter
+        opts.switch_res = a.switch_res
+        opts.use_graph = 0 if a.no_graph else 1
+        times = []
+        for i in range(a.warmup + a.iters):
+            phi.copy_(phi0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep = ctx.pcg_solve(phi, opts)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= a.warmup:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        print(json.dumps({"op": "solve", "workload": a.workload, "prec": a.prec, "max_iter": a.max_iter,
+                          "graph": not a.no_graph, "iters": rep["iters"], "iters_lo": rep["iters_lo"], "ms": ms,
+                          "ms_per_iter": ms / max(rep["iters"], 1)}))
+        return
+
+    n = tuple(a.grid)
+    N = int(np.prod(n))
+    L = (a.L,) * len(n)
+    V = torch.zeros(N, dtype=torch.float64, device=dev)
+    ctx = gpe.Context(n, L, 100.0, 0.5, V, prec=prec)
+    del V
+    dt = torch.complex128 if a.prec == "fp64" else torch.complex64
+    g = torch.Generator(device=dev).manual_seed(1)
+    phi = torch.randn(N, dtype=dt, device=dev, generator=g)
+    out = torch.empty_like(phi)
+    cb = 16 if a.prec == "fp64" else 8
+    vb = 8 if a.prec == "fp64" else 4
+    if a.op == "apply_H":
+        call = lambda: ctx.apply_H(phi, phi, out)  # noqa: E731
+        bytes_pt = 2 * cb + vb
+    elif a.op == "precond":
+        call = lambda: ctx.precond(phi, phi, 1.5, out)  # noqa: E731
+        bytes_pt = 3 * cb + vb
+    else:
+        call = lambda: ctx.energy(phi)  # noqa: E731
+        bytes_pt = cb + vb
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    print(json.dumps({"op": a.op, "grid": list(n), "prec": a.prec, "points": N, "ms": ms,
+                      "algorithmic_bytes_per_point": bytes_pt,
+                      "effective_GBps": bytes_pt * N / (ms * 1e-3) / 1e9}))
+
+
+if __name__ == "__main__":
+    main()
