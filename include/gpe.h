@@ -163,6 +163,35 @@ gpe_status gpe_energy(gpe_ctx* ctx, const void* phi_dev, double out[8]);
  * GPE_ERR_CUDA (report->status carries the same code). */
 gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* opts, gpe_report* report);
 
+/* Allocation-free H_phi f.  The paper has no counterpart: this is an
+ * interface addition for callers that cannot allocate device memory --
+ * code running under a memory manager that owns the whole device, inside a
+ * library that promised never to call the allocator, or with the device
+ * memory already exhausted -- and so cannot create a context.
+ *
+ * Computes the same out = H_phi f as gpe_apply_H, with the same kernels, but
+ * takes the problem directly and keeps its intermediate field, grid tables,
+ * reduction partials and control block in one fixed static device array of
+ * libgpe (about 17 MiB, held by every GPU that loads the library until the
+ * process exits).  It calls no cudaMalloc/cudaFree and no allocating library.
+ *  prob    : as for gpe_create; prob->prec selects the element types.
+ *  V_dev   : real potential on the device, float64 for GPE_FP64, float32 for
+ *            GPE_MIXED, [z][y][x].
+ *  phi_dev, f_dev, out_dev : device fields, complex128 (GPE_FP64) or
+ *            complex64 (GPE_MIXED); out may alias f.
+ *  stream  : cudaStream_t ordering the work (NULL = legacy default stream).
+ *  err, err_len : optional buffer for a message (NUL-terminated), may be NULL.
+ * Limit: N * sizeof(element) <= 16 MiB, i.e. at most 2^20 complex128 or 2^21
+ * complex64 points; larger grids return GPE_ERR_UNSUPPORTED with the sizes in
+ * err.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array and leaves its last contents there, so
+ * calls whose GPU work can overlap (other streams, other host threads) race:
+ * serialise them.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED,
+ * GPE_ERR_CUDA. */
+gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V_dev, const void* phi_dev, const void* f_dev,
+                               void* out_dev, void* stream, char* err, size_t err_len);
+
 /* Human-readable description of the last failure on ctx ("" if none).
  * The string is owned by ctx and valid until its next call. ctx NULL gives
  * the message of the last failed gpe_create. */
