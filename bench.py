@@ -230,7 +230,11 @@ def main():
     launches = 0
     for r in reps:
         it, lo = r["iters"], r["iters_lo"]
-        launches += 2 + (1 + 7 * (lo + 1)) + (1 + 7 * (it - lo + 1))
+        if r["loop_kind"] == 2:
+            # two precision conversions; per phase one normalisation kernel and one persistent solve kernel
+            launches += 2 + 2 + 2
+        else:
+            launches += 2 + (1 + 7 * (lo + 1)) + (1 + 7 * (it - lo + 1))
 
     # ---------------- e2e: phi in pinned host memory ----------------
     phi_h0 = torch.from_numpy(w["phi0"].copy()).pin_memory()
@@ -320,6 +324,7 @@ def main():
             "config": {"workload": WORKLOAD, "grid": "256x256", "domain": "[-16,16]^2", "eta": 1000.0,
                        "omega": 0.9, "V": "r^2/2", "precision": "mixed (c64 phase, c128 refinement)",
                        "tol_res_inf": 1e-8, "iters": last["iters"], "iters_c64": last["iters_lo"],
+                       "loop": {2: "persistent kernel", 1: "graph", 0: "host loop"}[last["loop_kind"]],
                        "E": last["E"], "res_inf": last["res_inf"],
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

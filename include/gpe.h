@@ -83,7 +83,11 @@ typedef struct {
   int stall_window;     /* [500] */
   double switch_res;    /* [0: automatic] */
   int max_iter_lo;      /* cap on complex64-phase iterations [max_iter] */
-  int use_graph;        /* 1: one CUDA graph launch with a device-side loop; 0: host loop [1] */
+  int use_graph;        /* how the iteration loop runs [2]:
+                         * 2: one persistent cooperative kernel for the whole loop (square 2D grids with
+                         *    n in [64,512], cubic 3D grids with n in [64,256]; others fall back to 1);
+                         * 1: one CUDA graph launch whose WHILE node repeats the per-pass kernels;
+                         * 0: the per-pass kernels launched from a host loop. */
 } gpe_solve_opts;
 
 /* Per-iteration log row, doubles: */
@@ -106,6 +110,7 @@ typedef struct {
   int log_cap;       /* in: rows available in log (0: no log) */
   int log_len;       /* out: rows written (min(iters + 1, log_cap)) */
   double* log;       /* in: host array [log_cap][GPE_LOG_FIELDS] or NULL */
+  int loop_kind;     /* out: loop style of the last phase: 2 persistent kernel, 1 graph, 0 host loop */
 } gpe_report;
 
 typedef struct gpe_ctx gpe_ctx;

@@ -6,12 +6,14 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/gpe.h"
 #include "gpe_internal.h"
+#include "gpe_persist.cuh"
 
 using namespace gpe;
 
@@ -62,6 +64,11 @@ struct gpe_ctx {
   double vmax = 0.0;  // max V on the grid
   int max_threads[2] = {512, 256};
   bool warmed[3] = {false, false, false};
+  int nsm = 0;                      // streaming multiprocessors of the device
+  double* pers_partials = nullptr;  // persistent solve: [2][grid][kMaxMoments]
+  unsigned* pers_bar = nullptr;     // persistent solve: barrier words + error flag
+  int pers_max_grid = 0;
+  int last_loop = -1;  // loop style the last solve phase ran (gpe_report.loop_kind)
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // per launch mode
 };
 
@@ -214,6 +221,7 @@ static void free_ctx(gpe_ctx* c) {
     for (int i = 0; i < 3; ++i) { cudaFree(b.xi[i]); cudaFree(b.xc[i]); cudaFree(b.tw[i]); }
     cudaFree(b.V); cudaFree(b.phi); cudaFree(b.p); cudaFree(b.t); cudaFree(b.s); cudaFree(b.r_prev);
   }
+  cudaFree(c->pers_partials); cudaFree(c->pers_bar);
   cudaFree(c->ctl_solve); cudaFree(c->ctl_api); cudaFree(c->partials); cudaFree(c->ticket); cudaFree(c->log_dev);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
@@ -230,7 +238,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->stall_window = 500;
   o->switch_res = 0.0;
   o->max_iter_lo = 0;
-  o->use_graph = 1;
+  o->use_graph = 2;
   return GPE_OK;
 }
 
@@ -294,6 +302,16 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
       cudaMalloc(&c->partials, sizeof(double) * kMaxMoments * (size_t)maxblocks) != cudaSuccess ||
       cudaMalloc(&c->ticket, sizeof(unsigned)) != cudaSuccess) {
     c->err = "cudaMalloc workspace"; return fail(GPE_ERR_CUDA);
+  }
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->pers_max_grid = 8 * (c->nsm > 0 ? c->nsm : 1);
+    if (cudaMalloc(&c->pers_partials, sizeof(double) * 2 * kMaxMoments * (size_t)c->pers_max_grid) != cudaSuccess ||
+        cudaMalloc(&c->pers_bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+      c->err = "cudaMalloc persistent workspace"; return fail(GPE_ERR_CUDA);
+    }
   }
   cudaMemset(c->ctl_solve, 0, sizeof(Ctl));
   cudaMemset(c->ctl_api, 0, sizeof(Ctl));
@@ -387,34 +405,143 @@ extern "C" gpe_status gpe_precond(gpe_ctx* c, const void* phi, const void* r, do
   return run_PC(c, b, r, alpha, out, c->ctl_api, false, c->st);
 }
 
-// One PCG iteration (all passes) in launch mode `mode`, on the solver buffers.
-static gpe_status enqueue_iteration(gpe_ctx* c, int mode, cudaStream_t st, unsigned long long cond) {
+// The pass arguments of one PCG iteration in launch mode `mode`, on the solver
+// buffers (default plans: one unit per block).
+struct IterArgs {
+  PassArgs hx, hmid[2], c1, cfwd, ccore, cinv, c3, ax, amid[2];
+};
+
+static IterArgs iter_args(gpe_ctx* c, int mode, unsigned long long cond) {
   const IterBufs b = iter_bufs(c, mode);
   Ctl* ctl = c->ctl_solve;
+  IterArgs I;
   // H phi (with the retraction phi_{n+1} = (c phi_n + s p_n/|p_n|)/nrm folded into the x pass)
-  PassArgs a = base_args(c, b.tab_h, 0);
-  a.V = b.V;
-  a.ctl = ctl; a.solver = 1; a.phi = b.phi; a.phi_out = b.phi; a.p = b.p; a.t = b.t;
-  GPE_CU(c, launch(mode, P_HX, a, st));
-  for (int ax = 1; ax < c->dim; ++ax) {
-    PassArgs h = base_args(c, b.tab_h, ax);
+  I.hx = base_args(c, b.tab_h, 0);
+  I.hx.V = b.V;
+  I.hx.ctl = ctl; I.hx.solver = 1; I.hx.phi = b.phi; I.hx.phi_out = b.phi; I.hx.p = b.p; I.hx.t = b.t;
+  for (int ax = 1; ax < 3; ++ax) {
+    PassArgs& h = I.hmid[ax - 1];
+    h = base_args(c, b.tab_h, ax < c->dim ? ax : 0);
     h.ctl = ctl; h.solver = 1; h.phi = b.phi; h.t = b.t; h.last_axis = (ax == c->dim - 1);
-    GPE_CU(c, launch(mode, P_HMID, h, st));
   }
   // P_C r_n
-  gpe_status s = run_PC(c, b, nullptr, 0.0, nullptr, ctl, true, st);
-  if (s != GPE_OK) return s;
+  I.c1 = base_args(c, b.tab_d, 0);
+  I.c1.V = b.V;
+  I.c1.ctl = ctl; I.c1.solver = 1; I.c1.phi = b.phi; I.c1.s = b.s; I.c1.t = b.t; I.c1.r_prev = b.r_prev; I.c1.p = b.p;
+  I.c3 = I.c1;
+  const int ay = c->dim == 3 ? 1 : 0;
+  I.cfwd = base_args(c, b.tab_d, ay);
+  I.cfwd.ctl = ctl; I.cfwd.solver = 1; I.cfwd.s = b.s;
+  I.cinv = I.cfwd;
+  I.ccore = base_args(c, b.tab_d, c->dim - 1);
+  I.ccore.ctl = ctl; I.ccore.solver = 1; I.ccore.s = b.s;
   // p_n and the step-size moments
-  PassArgs x = base_args(c, b.tab_d, 0);
-  x.V = b.V;
-  x.ctl = ctl; x.solver = 1; x.phi = b.phi; x.s = b.s; x.t = b.t; x.p = b.p;
-  GPE_CU(c, launch(mode, P_AX, x, st));
-  for (int ax = 1; ax < c->dim; ++ax) {
-    PassArgs m = base_args(c, b.tab_d, ax);
+  I.ax = base_args(c, b.tab_d, 0);
+  I.ax.V = b.V;
+  I.ax.ctl = ctl; I.ax.solver = 1; I.ax.phi = b.phi; I.ax.s = b.s; I.ax.t = b.t; I.ax.p = b.p;
+  for (int ax = 1; ax < 3; ++ax) {
+    PassArgs& m = I.amid[ax - 1];
+    m = base_args(c, b.tab_d, ax < c->dim ? ax : 0);
     m.ctl = ctl; m.solver = 1; m.phi = b.phi; m.p = b.p; m.last_axis = (ax == c->dim - 1);
     m.cond = m.last_axis ? cond : 0ull;
-    GPE_CU(c, launch(mode, P_AMID, m, st));
   }
+  return I;
+}
+
+// One PCG iteration (all passes) in launch mode `mode` as separate launches.
+static gpe_status enqueue_iteration(gpe_ctx* c, int mode, cudaStream_t st, unsigned long long cond) {
+  const IterArgs I = iter_args(c, mode, cond);
+  GPE_CU(c, launch(mode, P_HX, I.hx, st));
+  for (int ax = 1; ax < c->dim; ++ax) GPE_CU(c, launch(mode, P_HMID, I.hmid[ax - 1], st));
+  GPE_CU(c, launch(mode, P_C1, I.c1, st));
+  if (c->dim == 3) GPE_CU(c, launch(mode, P_CFWD, I.cfwd, st));
+  GPE_CU(c, launch(mode, P_CCORE, I.ccore, st));
+  if (c->dim == 3) GPE_CU(c, launch(mode, P_CINV, I.cinv, st));
+  GPE_CU(c, launch(mode, P_C3, I.c3, st));
+  GPE_CU(c, launch(mode, P_AX, I.ax, st));
+  for (int ax = 1; ax < c->dim; ++ax) GPE_CU(c, launch(mode, P_AMID, I.amid[ax - 1], st));
+  return GPE_OK;
+}
+
+// Square (2D, n in {64..512}) and cubic (3D, n in {64, 128, 256}) grids run the
+// whole loop in one persistent cooperative kernel.
+static bool persist_eligible(const gpe_ctx* c) {
+  const int M = c->n[0];
+  if (c->n[1] != M) return false;
+  if (c->dim == 2) return M >= 64 && M <= 512;
+  return c->n[2] == M && M >= 64 && M <= 256;
+}
+
+static cudaError_t launch_persist(int mode, int M, int dim, const PersistArgs& P, int grid, int block, size_t smem,
+                                  cudaStream_t st, int* mb) {
+  if (mode == 0) return launch_persist_m0(M, dim, P, grid, block, smem, st, mb);
+  if (mode == 1) return launch_persist_m1(M, dim, P, grid, block, smem, st, mb);
+  return launch_persist_m2(M, dim, P, grid, block, smem, st, mb);
+}
+
+// Launch the persistent solve for one phase.  *launched = false when the
+// kernel cannot be made co-resident (the caller falls back to the graph).
+static gpe_status run_persistent(gpe_ctx* c, int mode, bool* launched) {
+  *launched = false;
+  const int M = c->n[0];
+  const int Tl = M / 8;
+  const long long nlines = (long long)c->n[1] * (c->dim == 3 ? c->n[2] : 1);
+  // lines (x) or columns (y, z) per work unit: enough units for one block per
+  // SM (FP64 passes are bound by the per-SM FP64 rate), at most 256 threads
+  int g = 1;
+  while (2 * g * Tl <= 256 && nlines / (2 * g) >= c->nsm) g *= 2;
+  if (const char* ev = getenv("GPE_PERSIST_LINES")) {
+    const int v = atoi(ev);
+    if (v >= 1 && v * Tl <= 256 && (v & (v - 1)) == 0 && v <= nlines && v <= c->n[0]) g = v;
+  }
+  if (g * Tl < 32 && 32 / Tl <= nlines && 32 / Tl <= c->n[0]) g = 32 / Tl;  // at least one warp
+  const int block = g * Tl;
+  IterArgs I = iter_args(c, mode, 0ull);
+  const long long units = nlines / g;
+  auto setx = [&](PassArgs& a) { a.lpb = g; a.nblocks = (int)units; };
+  auto sets = [&](PassArgs& a, int axis) {
+    a.tx = g; a.ntx = c->n[0] / g;
+    a.nblocks = (int)units;
+    a.stride = (axis == 1) ? c->n[0] : (long long)c->n[0] * c->n[1];
+    a.outer_stride = (axis == 1) ? (long long)c->n[0] * c->n[1] : c->n[0];
+  };
+  PersistArgs P;
+  std::memset(&P, 0, sizeof(P));
+  P.hx = I.hx; setx(P.hx);
+  P.hy = I.hmid[0]; sets(P.hy, 1);
+  P.hz = I.hmid[1]; if (c->dim == 3) sets(P.hz, 2);
+  P.c1 = I.c1; setx(P.c1);
+  P.c3 = I.c3; setx(P.c3);
+  P.cfwd = I.cfwd; if (c->dim == 3) sets(P.cfwd, 1);
+  P.cinv = I.cinv; if (c->dim == 3) sets(P.cinv, 1);
+  P.ccore = I.ccore; sets(P.ccore, c->dim - 1);
+  P.ax = I.ax; setx(P.ax);
+  P.ay = I.amid[0]; sets(P.ay, 1);
+  P.az = I.amid[1]; if (c->dim == 3) sets(P.az, 2);
+  P.ctl = c->ctl_solve;
+  P.partials = c->pers_partials;
+  P.bar = c->pers_bar;
+  P.err = reinterpret_cast<int*>(c->pers_bar + 2);
+  P.units = units;
+  // dynamic shared memory: the larger of an x unit and a y/z unit, in the
+  // widest transform type of this mode
+  const size_t csz = (mode == 0) ? 8 : 16;
+  const size_t smx = (size_t)g * (M + M / 16) * csz, sms = (size_t)M * g * csz;
+  const size_t smem = smx > sms ? smx : sms;
+  int mb = 0;
+  cudaError_t e = launch_persist(mode, M, c->dim, P, 0, block, smem, c->st, &mb);
+  if (e != cudaSuccess || mb <= 0) {
+    cudaGetLastError();
+    c->err = std::string("persistent kernel not co-resident, graph loop used: ") +
+             (e != cudaSuccess ? cudaGetErrorString(e) : "occupancy 0");
+    return GPE_OK;
+  }
+  long long grid = (long long)mb * c->nsm;
+  if (grid > units) grid = units;
+  if (grid > c->pers_max_grid) grid = c->pers_max_grid;
+  GPE_CU(c, cudaMemsetAsync(c->pers_bar, 0, 4 * sizeof(unsigned), c->st));
+  GPE_CU(c, launch_persist(mode, M, c->dim, P, (int)grid, block, smem, c->st, nullptr));
+  *launched = true;
   return GPE_OK;
 }
 
@@ -468,7 +595,14 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
   GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, sbytes, c->st));
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
   GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->st));
-  if (o.use_graph) {
+  bool done_launch = false;
+  if (o.use_graph == 2 && persist_eligible(c)) {
+    s = run_persistent(c, mode, &done_launch);
+    if (s != GPE_OK) return s;
+  }
+  c->last_loop = done_launch ? 2 : (o.use_graph ? 1 : 0);
+  if (done_launch) {
+  } else if (o.use_graph) {
     s = build_graph(c, mode);
     if (s != GPE_OK) return s;
     GPE_CU(c, cudaGraphLaunch(c->exec[mode], c->st));
@@ -560,6 +694,7 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
     rep->status = h.status; rep->iters = h.iter; rep->iters_lo = iters_lo;
     rep->fallbacks = h.fallbacks; rep->backtracks = h.backtracks_total;
     rep->E = h.E; rep->lambda = h.lam; rep->res_inf = h.res_inf; rep->res_l2 = h.res_l2;
+    rep->loop_kind = c->last_loop;
     rep->log_len = 0;
     if (log_cap) {
       int nrows = h.iter + 1 < log_cap ? h.iter + 1 : log_cap;

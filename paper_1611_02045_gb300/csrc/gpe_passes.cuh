@@ -39,25 +39,62 @@ template <int M> struct LineCfg {
 };
 
 // ---------------------------------------------------------------------------
-// Reductions: K per-thread values -> per-block partial -> last block total.
-// MAXMASK bit k set: slot k is reduced with max instead of sum.
-// Returns true in every thread of the last block, with tot[] valid in
-// thread 0.
+// Reductions.
+//
+// Sums are accumulated in double-single arithmetic: an unevaluated pair of
+// FP32 numbers (hi, lo), added with Knuth's TwoSum error-free transformation
+// (D. E. Knuth, TAOCP vol. 2, 4.2.2) followed by a fast renormalisation
+// (T. J. Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18, 1971).  The pair carries ~48 significant bits
+// (relative error ~2^-47 per addition), so sums of FP32 terms lose nothing
+// and sums of FP64 terms lose ~1e-14 relative.  On GB300 an FP64 warp
+// instruction occupies the FP64 pipe ~64x longer than an FP32 one, so the
+// pair arithmetic keeps the many-level block and grid reductions off that
+// pipe; totals are converted to FP64 once, for the scalar steps.
+// Slots flagged in MAXMASK take the maximum instead (of non-negative values).
 // ---------------------------------------------------------------------------
-template <int K, unsigned MAXMASK>
-__device__ __forceinline__ double red_op(double a, double b, int k) {
-  return ((MAXMASK >> k) & 1u) ? fmax(a, b) : a + b;
+struct Acc {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Acc acc_from(float x) { return Acc{x, 0.0f}; }
+__device__ __forceinline__ Acc acc_from(double x) {
+  const float h = (float)x;
+  return Acc{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double acc_to_double(Acc a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ Acc acc_add(Acc a, Acc b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);  // TwoSum: s + e = a.hi + b.hi exactly
+  e += a.lo + b.lo;
+  const float h = s + e;                      // renormalise (|e| <= ulp(s))
+  return Acc{h, e - (h - s)};
+}
+__device__ __forceinline__ Acc acc_max(Acc a, Acc b) {
+  return (b.hi > a.hi || (b.hi == a.hi && b.lo > a.lo)) ? b : a;
 }
 
+template <unsigned MAXMASK>
+__device__ __forceinline__ Acc red_op(Acc a, Acc b, int k) {
+  return ((MAXMASK >> k) & 1u) ? acc_max(a, b) : acc_add(a, b);
+}
+
+__device__ __forceinline__ Acc shfl_acc(unsigned mask, Acc v, int o) {
+  return Acc{__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o)};
+}
+
+// Block total of v[k] (fixed tree); valid in thread 0 on return.
 template <int K, unsigned MAXMASK>
-__device__ __forceinline__ void block_reduce(double (&v)[K], double* red_sm) {
+__device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
   // blockDim.x is a power of two: either a multiple of 32 or one partial warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   const int width = blockDim.x < 32 ? (int)blockDim.x : 32;
   const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    for (int o = width >> 1; o > 0; o >>= 1) v[k] = red_op<K, MAXMASK>(v[k], __shfl_xor_sync(mask, v[k], o), k);
+    for (int o = width >> 1; o > 0; o >>= 1) v[k] = red_op<MAXMASK>(v[k], shfl_acc(mask, v[k], o), k);
   }
   __syncthreads();
   if (lane == 0) {
@@ -68,21 +105,27 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* red_sm) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double acc = red_sm[k];
-      for (int w = 1; w < nw; ++w) acc = red_op<K, MAXMASK>(acc, red_sm[w * K + k], k);
-      v[k] = acc;
+      Acc a = red_sm[k];
+      for (int w = 1; w < nw; ++w) a = red_op<MAXMASK>(a, red_sm[w * K + k], k);
+      v[k] = a;
     }
   }
 }
 
+// Partials live in a double-sized slot each (an Acc is 8 bytes).
+__device__ __forceinline__ Acc* acc_slots(double* p) { return reinterpret_cast<Acc*>(p); }
+
+// Per-block partials, then the last block to finish sums them in a fixed
+// order.  Returns true in the last block, with tot[] (FP64) valid in thread 0.
 template <int K, unsigned MAXMASK>
-__device__ __forceinline__ bool grid_reduce(double (&v)[K], const PassArgs& a, double (&tot)[K]) {
-  __shared__ double red_sm[32 * K];
+__device__ __forceinline__ bool grid_reduce(Acc (&v)[K], const PassArgs& a, double (&tot)[K]) {
+  __shared__ Acc red_sm[32 * K];
   __shared__ int s_last;
   block_reduce<K, MAXMASK>(v, red_sm);
+  Acc* part = acc_slots(a.partials);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) a.partials[(size_t)blockIdx.x * kMaxMoments + k] = v[k];
+    for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * kMaxMoments + k] = v[k];
     __threadfence();
     const unsigned prev = atomicAdd(a.ticket, 1u);
     s_last = (prev == gridDim.x - 1) ? 1 : 0;
@@ -90,21 +133,24 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const PassArgs& a, d
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double w[K];
+  Acc w[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) w[k] = 0.0;  // all slots hold non-negative values or sums
-  // L2-coherent loads (__ldcg), unrolled so that several blocks' partials are
-  // in flight at once; the summation order stays fixed.
+  for (int k = 0; k < K; ++k) w[k] = Acc{0.0f, 0.0f};
+  // L2-coherent loads, unrolled so that several blocks' partials are in
+  // flight at once; the summation order stays fixed.
 #pragma unroll 4
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double* pb = a.partials + (size_t)b * kMaxMoments;
+    const float2* pb = reinterpret_cast<const float2*>(part + (size_t)b * kMaxMoments);
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = red_op<K, MAXMASK>(w[k], __ldcg(pb + k), k);
+    for (int k = 0; k < K; ++k) {
+      const float2 x = __ldcg(pb + k);
+      w[k] = red_op<MAXMASK>(w[k], Acc{x.x, x.y}, k);
+    }
   }
   block_reduce<K, MAXMASK>(w, red_sm);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) tot[k] = w[k];
+    for (int k = 0; k < K; ++k) tot[k] = acc_to_double(w[k]);
     *a.ticket = 0u;  // ready for the next pass
   }
   return true;
@@ -113,13 +159,21 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const PassArgs& a, d
 // ---------------------------------------------------------------------------
 // Scalar steps (run by one thread of the last block)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double* log_row(Ctl* c) {
-  return (c->log && c->iter < c->log_cap) ? c->log + (size_t)c->iter * kLogFields : nullptr;
+// Constants the scalar steps need (from the pass arguments).
+struct Fin {
+  double weight, eta;
+  int dim, solver;
+};
+
+__device__ __forceinline__ Fin fin_of(const PassArgs& a) { return Fin{a.weight, a.eta, a.dim, a.solver}; }
+
+// Row n of the iteration log, or null (no log, full, or not the writing block).
+__device__ __forceinline__ double* log_row(Ctl* c, bool writer) {
+  return (writer && c->log && c->iter < c->log_cap) ? c->log + (size_t)c->iter * kLogFields : nullptr;
 }
 
 // After the last H pass: energy terms, lambda_n, lambda~_n, E_n (Section 2, eq. Opt_Alpha).
-static __device__ void finalize_H(const PassArgs& a) {
-  Ctl* c = a.ctl;
+static __device__ void finalize_H(Ctl* c, const Fin& a, bool writer) {
   const double w = a.weight;
   double kin = 0.0, rot = 0.0;
   for (int ax = 0; ax < a.dim; ++ax) { kin += c->hsum[ax][0]; rot += c->hsum[ax][1]; }
@@ -134,7 +188,7 @@ static __device__ void finalize_H(const PassArgs& a) {
   c->alpha = c->kin + c->pot + a.eta * c->U0;              // lambda~ (no rotation term)
   c->E = quad + 0.5 * a.eta * c->U0;
   if (a.solver) {
-    double* row = log_row(c);
+    double* row = log_row(c, writer);
     if (row) {
       row[0] = c->iter; row[1] = c->phase; row[2] = c->E; row[3] = c->lam;
       row[6] = c->alpha;
@@ -146,11 +200,10 @@ static __device__ void finalize_H(const PassArgs& a) {
 
 // After C1: residual norms and the stopping rule (eq. Stop_Residual), the
 // iteration cap, the optional energy rule, and (mixed phase) stall detection.
-static __device__ void finalize_C1(const PassArgs& a, const double (&tot)[3]) {
-  Ctl* c = a.ctl;
+static __device__ void finalize_C1(Ctl* c, const Fin& a, const double (&tot)[3], bool writer) {
   c->res_inf = sqrt(tot[0]);
   c->res_l2 = sqrt(a.weight * tot[1]);
-  double* row = log_row(c);
+  double* row = log_row(c, writer);
   if (row) { row[4] = c->res_inf; row[5] = c->res_l2; }
   const int nphase = c->iter - c->iter_phase0;
   if (!isfinite(c->E) || !isfinite(c->res_inf) || !isfinite(c->lam)) {
@@ -178,8 +231,7 @@ static __device__ void finalize_C1(const PassArgs& a, const double (&tot)[3]) {
 // descent check of Section 5.2 (Re<grad E, p> >= 0 -> gradient step).
 // tot: 0 <r,Pr>, 1 Re<r - r_prev, Pr>, 2 Re<Pr,phi>, 3 Re<p_prev,phi>,
 //      4 Re<r,p_prev>, 5 Re<r,phi>
-static __device__ void finalize_C3(const PassArgs& a, const double (&tot)[6]) {
-  Ctl* c = a.ctl;
+static __device__ void finalize_C3(Ctl* c, const Fin& a, const double (&tot)[6], bool writer) {
   const double w = a.weight;
   const double rPr = w * tot[0];
   double beta = 0.0;
@@ -195,15 +247,27 @@ static __device__ void finalize_C3(const PassArgs& a, const double (&tot)[6]) {
   }
   c->beta = beta; c->gamma = gamma; c->rPr = rPr;
   c->rPr_prev = rPr;
-  double* row = log_row(c);
+  double* row = log_row(c, writer);
   if (row) { row[7] = beta; row[10] = c->fallback; }
 }
 
-// Energy change along the geodesic, exact trigonometric polynomial (reading R6).
-__device__ __forceinline__ double delta_E(double th, double R, double aqq, double lam, double eta,
+// sin and cos of a step angle.  Steps are usually tiny, so for |t| < 0.05
+// the Maclaurin series (truncation below 1e-18 there: t^9/9! and t^10/10!)
+// replaces the general FP64 sincos, which is long on GB300's FP64 pipe.
+__device__ __forceinline__ void step_sincos(double t, double* s, double* c) {
+  if (fabs(t) < 0.05) {
+    const double t2 = t * t;
+    *s = t * (1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880)))));
+    *c = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24 + t2 * (-1.0 / 720 + t2 * (1.0 / 40320 + t2 * (-1.0 / 3628800)))));
+  } else {
+    sincos(t, s, c);
+  }
+}
+
+// Energy change along the geodesic, exact trigonometric polynomial (reading R6),
+// for s = sin(theta), c = cos(theta).
+__device__ __forceinline__ double delta_E(double s, double cth, double R, double aqq, double lam, double eta,
                                           double U0, double U1, double V2, double UW, double VW, double W2) {
-  double s, cth;
-  sincos(th, &s, &cth);
   const double s2 = s * s, c2 = cth * cth;
   return 2.0 * cth * s * R + s2 * (aqq - lam) +
          0.5 * eta * (s2 * s2 * (U0 + W2) + c2 * s2 * (4.0 * V2 + 2.0 * UW) + 4.0 * cth * s * s2 * (VW - U1));
@@ -215,8 +279,7 @@ __device__ __forceinline__ double delta_E(double th, double R, double aqq, doubl
 // asum[0]: 0 Re<H phi,p>, 1 <p,A_x p>+<p,V p>, 2 |p|^2, 3 u v, 4 v^2, 5 u w,
 //          6 v w, 7 w^2, 8 v    (u = |phi|^2, v = Re(conj(phi) p), w = |p|^2)
 // asum[ax>0][1]: <p, A_ax p>
-static __device__ void finalize_A(const PassArgs& a) {
-  Ctl* c = a.ctl;
+static __device__ void finalize_A(Ctl* c, const Fin& a, bool writer) {
   const double w = a.weight;
   const double* s0 = c->asum[0];
   const double W1 = w * s0[2];
@@ -231,18 +294,19 @@ static __device__ void finalize_A(const PassArgs& a) {
   const double eta = a.eta, lam = c->lam, U0 = c->U0;
   const double curv = aqq + eta * UW + 2.0 * eta * V2 - lam;
   double th = (curv > 0.0) ? -R / curv : c->theta_default;
-  double dE = delta_E(th, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
+  double sn, cs;
+  step_sincos(th, &sn, &cs);
+  double dE = delta_E(sn, cs, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
   int bt = 0;
   while (!(dE < 0.0) && bt < c->max_backtracks) {
     th *= 0.5; ++bt;
-    dE = delta_E(th, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
+    step_sincos(th, &sn, &cs);
+    dE = delta_E(sn, cs, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
   }
-  double sn, cs;
-  sincos(th, &sn, &cs);
   const double nrm2 = cs * cs * c->norm2 + 2.0 * cs * sn * rho + sn * sn;
   c->theta = th; c->c = cs; c->s = sn; c->inv_np = inv; c->inv_nrm = 1.0 / sqrt(nrm2);
   c->dE = dE; c->backtracks = bt; c->backtracks_total += bt;
-  double* row = log_row(c);
+  double* row = log_row(c, writer);
   if (row) { row[8] = th; row[9] = dE; row[11] = bt; }
   c->retract = 1;
   c->restart = 0;
@@ -254,6 +318,31 @@ static __device__ void finalize_A(const PassArgs& a) {
 __device__ __forceinline__ void set_loop_condition(const PassArgs& a, int keep_going) {
   if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, keep_going ? 1u : 0u);
 }
+
+// Scalars a pass body reads (copied from the control block at entry).
+struct Scal {
+  int retract;
+  double c, s, inv_np, inv_nrm, lam, alpha, beta, gamma;
+};
+
+__device__ __forceinline__ Scal scal_of(const Ctl* c, const PassArgs& a) {
+  Scal S;
+  S.retract = a.solver ? c->retract : 0;
+  S.c = c->c; S.s = c->s; S.inv_np = c->inv_np; S.inv_nrm = c->inv_nrm;
+  S.lam = a.solver ? c->lam : 0.0;
+  S.alpha = a.solver ? c->alpha : (a.api_alpha > 0 ? a.api_alpha : c->alpha);
+  S.beta = c->beta; S.gamma = c->gamma;
+  return S;
+}
+
+// Reduction slots per pass and which of them are maxima.
+template <int ROLE> struct Moments { static constexpr int K = 0; static constexpr unsigned MAX = 0u; };
+template <> struct Moments<P_HX> { static constexpr int K = 6; static constexpr unsigned MAX = 32u; };
+template <> struct Moments<P_HMID> { static constexpr int K = 2; static constexpr unsigned MAX = 0u; };
+template <> struct Moments<P_C1> { static constexpr int K = 3; static constexpr unsigned MAX = 1u; };
+template <> struct Moments<P_C3> { static constexpr int K = 6; static constexpr unsigned MAX = 0u; };
+template <> struct Moments<P_AX> { static constexpr int K = 9; static constexpr unsigned MAX = 0u; };
+template <> struct Moments<P_AMID> { static constexpr int K = 1; static constexpr unsigned MAX = 0u; };
 
 // ---------------------------------------------------------------------------
 // Multipliers
@@ -276,20 +365,21 @@ template <typename T> struct MaxThreads { static constexpr int value = sizeof(T)
 template <typename To, typename From>
 __device__ __forceinline__ cplx<To> cconv(From v) { return cmk<cplx<To>>((To)v.x, (To)v.y); }
 
+// One unit of a contiguous pass: lines unit*lpb .. unit*lpb + lpb - 1 (the
+// block has lpb * M/8 threads).  Adds this thread's reduction terms to acc[]
+// (Moments<ROLE>: sums, or maxima for the slots flagged in MAX).
 template <typename TF, typename TS, typename TD, int M, int ROLE>
-__global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
+__device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long long unit, unsigned char* smraw,
+                                      Acc* acc) {
   using CF = cplx<TF>;
   using CS = cplx<TS>;
   using CD = cplx<TD>;
   constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
   constexpr int LS = M + M / 16;  // padded line stride in shared memory
-  extern __shared__ __align__(16) unsigned char smraw[];
   CF* sm = reinterpret_cast<CF*>(smraw);
-  Ctl* ctl = a.ctl;
-  if (a.solver && ctl->done) return;
 
   const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
-  const long long line = (long long)blockIdx.x * a.lpb + l;
+  const long long line = unit * a.lpb + l;
   const long long base = line * M;
   const int iy = (int)(line % a.ny);
   const CF* __restrict__ tw = static_cast<const CF*>(a.tw);
@@ -305,9 +395,9 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
     const CS* __restrict__ f = static_cast<const CS*>(a.f ? a.f : a.phi);
     CS ph[E];
-    const bool retract = a.solver && ctl->retract;
-    const TS cc = TS(retract ? ctl->c * ctl->inv_nrm : 1.0);
-    const TS ss = TS(retract ? ctl->s * ctl->inv_np * ctl->inv_nrm : 0.0);
+    const bool retract = S.retract;
+    const TS cc = TS(retract ? S.c * S.inv_nrm : 1.0);
+    const TS ss = TS(retract ? S.s * S.inv_np * S.inv_nrm : 0.0);
     const CD* __restrict__ p = static_cast<const CD*>(a.p);
     CS* __restrict__ phi_out = static_cast<CS*>(a.phi_out);
 #pragma unroll
@@ -348,20 +438,18 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
       tout[g] = cmk<CS>(TS(v[q].x) + m * fq.x, TS(v[q].y) + m * fq.y);
       apot += vv * u; au2 += u * u; an2 += u; umax = fmax(umax, u);
     }
-    double acc[6] = {double(akin) * double(invM), double(arot) * double(invM), double(apot), double(au2), double(an2),
-                     double(umax)};
-    double tot[6];
-    if (grid_reduce<6, 32u>(acc, a, tot) && threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) ctl->hsum[0][k] = tot[k];
-    }
+    acc[0] = acc_add(acc[0], acc_from(akin * invM));
+    acc[1] = acc_add(acc[1], acc_from(arot * invM));
+    acc[2] = acc_add(acc[2], acc_from(apot));
+    acc[3] = acc_add(acc[3], acc_from(au2));
+    acc[4] = acc_add(acc[4], acc_from(an2));
+    acc[5] = acc_max(acc[5], acc_from(umax));
   } else if constexpr (ROLE == P_C1) {
     // ---- s = FFT_x[P_V^{1/2} r], r = H phi - lambda phi (solver) or r_in (API) ----
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
     const CS* __restrict__ rin = static_cast<const CS*>(a.solver ? a.t : a.r_in);
-    const TS lam = TS(a.solver ? ctl->lam : 0.0);
-    const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
-    const TS alpha = TS(alpha_d);
+    const TS lam = TS(S.lam);
+    const TS alpha = TS(S.alpha);
     const TS eta = TS(a.eta);
     TS rmax = 0, r2 = 0, bad = 0;
 #pragma unroll
@@ -380,11 +468,9 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
     CD* __restrict__ sout = static_cast<CD*>(a.s);
 #pragma unroll
     for (int q = 0; q < E; ++q) sout[base + t + q * Tl] = cconv<TD>(v[q]);
-    if (a.solver) {
-      double acc[3] = {double(rmax), double(r2), double(bad)};
-      double tot[3];
-      if (grid_reduce<3, 1u>(acc, a, tot) && threadIdx.x == 0) finalize_C1(a, tot);
-    }
+    acc[0] = acc_max(acc[0], acc_from(rmax));
+    acc[1] = acc_add(acc[1], acc_from(r2));
+    acc[2] = acc_add(acc[2], acc_from(bad));
   } else if constexpr (ROLE == P_C3) {
     // ---- Pr = P_V^{1/2} IFFT_x[s] (the 1/N is applied in the core pass) ----
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
@@ -392,8 +478,7 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = cconv<TF>(sbuf[base + t + q * Tl]);
     line_dft<M, E, +1>(v, sm, si, t, tw);
-    const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
-    const TS alpha = TS(alpha_d);
+    const TS alpha = TS(S.alpha);
     const TS eta = TS(a.eta);
     if (!a.solver) {
       CD* __restrict__ out = static_cast<CD*>(a.out);
@@ -409,7 +494,7 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
     const CS* __restrict__ Hphi = static_cast<const CS*>(a.t);
     CS* __restrict__ rprev = static_cast<CS*>(a.r_prev);
     const CD* __restrict__ pprev = static_cast<const CD*>(a.p);
-    const TS lam = TS(ctl->lam);
+    const TS lam = TS(S.lam);
     TS a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -431,16 +516,16 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
       a5 += r.x * ph.x + r.y * ph.y;
       rprev[g] = r;
     }
-    double acc[6] = {double(a0), double(a1), double(a2), double(a3), double(a4), double(a5)};
-    double tot[6];
-    if (grid_reduce<6, 0u>(acc, a, tot) && threadIdx.x == 0) finalize_C3(a, tot);
+    acc[0] = acc_add(acc[0], acc_from(a0)); acc[1] = acc_add(acc[1], acc_from(a1));
+    acc[2] = acc_add(acc[2], acc_from(a2)); acc[3] = acc_add(acc[3], acc_from(a3));
+    acc[4] = acc_add(acc[4], acc_from(a4)); acc[5] = acc_add(acc[5], acc_from(a5));
   } else if constexpr (ROLE == P_AX) {
     // ---- p = -Pr + beta p_prev - gamma phi ; moments for the step size ----
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
     const CD* __restrict__ Pr = static_cast<const CD*>(a.s);
     const CS* __restrict__ Hphi = static_cast<const CS*>(a.t);
     CD* __restrict__ pbuf = static_cast<CD*>(a.p);
-    const TS beta = TS(ctl->beta), gamma = TS(ctl->gamma);
+    const TS beta = TS(S.beta), gamma = TS(S.gamma);
     TS aR = 0, aV = 0, aW1 = 0, aUV = 0, aV2 = 0, aUW = 0, aVW = 0, aW2 = 0, aRho = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -467,35 +552,30 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
       const TF k = xi[t + q * Tl];
       akr += (TF(0.5) * k * k + om * y * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
     }
-    double acc[9] = {double(aR), double(aV) + double(akr) * double(invM), double(aW1), double(aUV), double(aV2),
-                     double(aUW), double(aVW), double(aW2), double(aRho)};
-    double tot[9];
-    if (grid_reduce<9, 0u>(acc, a, tot) && threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) ctl->asum[0][k] = tot[k];
-    }
+    acc[0] = acc_add(acc[0], acc_from(aR));
+    acc[1] = acc_add(acc_add(acc[1], acc_from(aV)), acc_from(akr * invM));
+    acc[2] = acc_add(acc[2], acc_from(aW1)); acc[3] = acc_add(acc[3], acc_from(aUV));
+    acc[4] = acc_add(acc[4], acc_from(aV2)); acc[5] = acc_add(acc[5], acc_from(aUW));
+    acc[6] = acc_add(acc[6], acc_from(aVW)); acc[7] = acc_add(acc[7], acc_from(aW2));
+    acc[8] = acc_add(acc[8], acc_from(aRho));
   }
 }
 
 // ---------------------------------------------------------------------------
 // Strided (y, z) passes.  Block = tx columns x Tl threads; tid = c + tx*t.
 // ---------------------------------------------------------------------------
+// One unit of a strided pass: the tile of tx adjacent x-columns number unit
+// (block = tx * M/8 threads).  Reduction terms are added to acc[].
 template <typename T, int M, int ROLE>
-__global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
+__device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long long unit, unsigned char* smraw,
+                                      Acc* acc) {
   using C = cplx<T>;
   constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
-  extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  Ctl* ctl = a.ctl;
-  const bool is_loop_tail = (ROLE == P_AMID) && a.last_axis;
-  if (a.solver && ctl->done) {
-    if (is_loop_tail && blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(a, 0);
-    return;
-  }
   const int tx = a.tx;
   const int c = threadIdx.x % tx, t = threadIdx.x / tx;
-  const int xt = blockIdx.x % a.ntx;
-  const long long outer = blockIdx.x / a.ntx;
+  const int xt = (int)(unit % a.ntx);
+  const long long outer = unit / a.ntx;
   const int ix = xt * tx + c;
   const long long base = outer * a.outer_stride + ix;
   const long long st = a.stride;
@@ -530,13 +610,8 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
       const long long g = base + (t + q * Tl) * st;
       dst[g] = cadd(tb[g], v[q]);
     }
-    double acc[2] = {double(akin) * double(invM), double(arot) * double(invM)};
-    double tot[2];
-    if (grid_reduce<2, 0u>(acc, a, tot) && threadIdx.x == 0) {
-      ctl->hsum[a.axis][0] = tot[0];
-      ctl->hsum[a.axis][1] = tot[1];
-      if (a.last_axis) finalize_H(a);
-    }
+    acc[0] = acc_add(acc[0], acc_from(akin * invM));
+    acc[1] = acc_add(acc[1], acc_from(arot * invM));
   } else if constexpr (ROLE == P_CFWD || ROLE == P_CINV || ROLE == P_CCORE) {
     C* __restrict__ sb = static_cast<C*>(a.s);
 #pragma unroll
@@ -548,8 +623,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
     }
     if constexpr (ROLE == P_CCORE) {
       // (alpha + |k|^2 / 2)^{-1} / N on the full frequency grid (eq. PDelta)
-      const double alpha_d = a.solver ? ctl->alpha : (a.api_alpha > 0 ? a.api_alpha : ctl->alpha);
-      const T alpha = T(alpha_d);
+      const T alpha = T(S.alpha);
       const T invN = T(1.0 / ((double)a.nx * a.ny * (a.dim == 3 ? a.nz : 1)));
       const T kx = tab<T>(a.xi[0])[ix];
       T kother = 0;
@@ -582,16 +656,80 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
       const T k = xia[t + q * Tl];
       akr += (T(0.5) * k * k + rs * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
     }
-    double acc[1] = {double(akr) * double(invM)};
-    double tot[1];
-    if (grid_reduce<1, 0u>(acc, a, tot) && threadIdx.x == 0) {
-      ctl->asum[a.axis][1] = tot[0];
-      if (a.last_axis) {
-        finalize_A(a);
-        set_loop_condition(a, ctl->done ? 0 : 1);
-      }
+    acc[0] = acc_add(acc[0], acc_from(akr * invM));
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Standalone pass kernels (one unit per block): used by the API entry points,
+// the graph-captured solve and the host-loop solve.  The last block to finish
+// sums the per-block partials in a fixed order and runs the scalar step.
+// ---------------------------------------------------------------------------
+template <int ROLE, int K>
+__device__ __forceinline__ void store_sums(const PassArgs& a, const double (&tot)[K]) {
+  Ctl* ctl = a.ctl;
+  const Fin F = fin_of(a);
+  if constexpr (ROLE == P_HX) {
+    for (int k = 0; k < K; ++k) ctl->hsum[0][k] = tot[k];
+  } else if constexpr (ROLE == P_HMID) {
+    ctl->hsum[a.axis][0] = tot[0];
+    ctl->hsum[a.axis][1] = tot[1];
+    if (a.last_axis) finalize_H(ctl, F, true);
+  } else if constexpr (ROLE == P_C1) {
+    finalize_C1(ctl, F, tot, true);
+  } else if constexpr (ROLE == P_C3) {
+    finalize_C3(ctl, F, tot, true);
+  } else if constexpr (ROLE == P_AX) {
+    for (int k = 0; k < K; ++k) ctl->asum[0][k] = tot[k];
+  } else if constexpr (ROLE == P_AMID) {
+    ctl->asum[a.axis][1] = tot[0];
+    if (a.last_axis) {
+      finalize_A(ctl, F, true);
+      set_loop_condition(a, ctl->done ? 0 : 1);
     }
   }
+}
+
+template <int ROLE>
+__device__ __forceinline__ void reduce_and_finish(const PassArgs& a, const Acc* acc) {
+  constexpr int K = Moments<ROLE>::K;
+  if constexpr (K > 0) {
+    // the P_C passes reduce only inside a solve
+    if ((ROLE == P_C1 || ROLE == P_C3) && !a.solver) return;
+    Acc v[K];
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = acc[k];
+    if (grid_reduce<K, Moments<ROLE>::MAX>(v, a, tot) && threadIdx.x == 0) store_sums<ROLE, K>(a, tot);
+  }
+}
+
+template <typename TF, typename TS, typename TD, int M, int ROLE>
+__global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.solver && a.ctl->done) return;
+  const Scal S = scal_of(a.ctl, a);
+  Acc acc[kMaxMoments];
+#pragma unroll
+  for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
+  xunit<TF, TS, TD, M, ROLE>(a, S, blockIdx.x, smraw, acc);
+  reduce_and_finish<ROLE>(a, acc);
+}
+
+template <typename T, int M, int ROLE>
+__global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.solver && a.ctl->done) {
+    if (ROLE == P_AMID && a.last_axis && blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(a, 0);
+    return;
+  }
+  const Scal S = scal_of(a.ctl, a);
+  Acc acc[kMaxMoments];
+#pragma unroll
+  for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
+  sunit<T, M, ROLE>(a, S, blockIdx.x, smraw, acc);
+  reduce_and_finish<ROLE>(a, acc);
 }
 
 // ---------------------------------------------------------------------------

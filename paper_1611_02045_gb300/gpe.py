@@ -42,7 +42,7 @@ class gpe_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("iters_lo", C.c_int), ("fallbacks", C.c_int),
                 ("backtracks", C.c_int), ("E", C.c_double), ("lambda_", C.c_double), ("res_inf", C.c_double),
                 ("res_l2", C.c_double), ("log_cap", C.c_int), ("log_len", C.c_int),
-                ("log", C.POINTER(C.c_double))]
+                ("log", C.POINTER(C.c_double)), ("loop_kind", C.c_int)]
 
 
 class GpeError(RuntimeError):
@@ -159,7 +159,8 @@ class Context:
             self._check(s)
         out = dict(status=rep.status, status_name=STATUS_NAMES.get(rep.status), iters=rep.iters,
                    iters_lo=rep.iters_lo, fallbacks=rep.fallbacks, backtracks=rep.backtracks, E=rep.E,
-                   lam=rep.lambda_, res_inf=rep.res_inf, res_l2=rep.res_l2)
+                   lam=rep.lambda_, res_inf=rep.res_inf, res_l2=rep.res_l2, loop_kind=rep.loop_kind,
+                   note=lib().gpe_last_error(self._ctx).decode())
         if logbuf is not None:
             out["log"] = logbuf[: rep.log_len].copy()
         return out

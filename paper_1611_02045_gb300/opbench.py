@@ -24,7 +24,8 @@ def main():
     ap.add_argument("--workload", default="fast256_2d", help="for --op solve")
     ap.add_argument("--max-iter", type=int, default=50, help="for --op solve")
     ap.add_argument("--switch-res", type=float, default=0.0, help="for --op solve (mixed)")
-    ap.add_argument("--no-graph", action="store_true", help="for --op solve: host-driven loop")
+    ap.add_argument("--loop", choices=["persistent", "graph", "host"], default="persistent",
+                    help="for --op solve: persistent kernel, graph with device-side loop, or host loop")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -45,7 +46,7 @@ def main():
         opts = gpe.solve_opts_default()
         opts.max_iter = a.max_iter
         opts.switch_res = a.switch_res
-        opts.use_graph = 0 if a.no_graph else 1
+        opts.use_graph = {"persistent": 2, "graph": 1, "host": 0}[a.loop]
         times = []
         for i in range(a.warmup + a.iters):
             phi.copy_(phi0)
@@ -58,7 +59,7 @@ def main():
                 times.append(e0.elapsed_time(e1))
         ms = statistics.median(times)
         print(json.dumps({"op": "solve", "workload": a.workload, "prec": a.prec, "max_iter": a.max_iter,
-                          "graph": not a.no_graph, "iters": rep["iters"], "iters_lo": rep["iters_lo"], "ms": ms,
+                          "loop": a.loop, "loop_kind": rep["loop_kind"], "iters": rep["iters"], "iters_lo": rep["iters_lo"], "ms": ms,
                           "ms_per_iter": ms / max(rep["iters"], 1)}))
         return
 

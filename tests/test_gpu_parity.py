@@ -155,7 +155,7 @@ def _workload_problem(name):
     return w, O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("use_graph", [2, 1, 0], ids=["persistent", "graph", "hostloop"])
 def test_pcg_per_iterate_parity_fp64(G, use_graph):
     """Same seeded phi_0, FP64: E_n (rel 1e-12) and phi_n (phase-aligned L2 1e-9)
     over the first 20 iterations; beta_n, theta_n and the discrete decisions agree."""
@@ -169,6 +169,7 @@ def test_pcg_per_iterate_parity_fp64(G, use_graph):
             o.max_iter = k
             o.use_graph = use_graph
             rep = ctx.pcg_solve(phi, o, log_cap=64)
+            assert rep["loop_kind"] == use_graph, rep["note"]
             assert rep["iters"] == k and rep["status"] == G.GPE_ERR_NOT_CONVERGED
             assert phase_aligned_rel_l2(host(phi), orep["iterates"][k]) < 1e-9, k
         log = rep["log"]
@@ -239,6 +240,46 @@ def test_pcg_3d_per_iterate_and_converged(G):
     assert abs(rep["E"] - oconv["E"]) <= 1e-10 * abs(oconv["E"])
 
 
+@pytest.mark.parametrize("use_graph", [2, 1], ids=["persistent", "graph"])
+def test_pcg_3d_per_iterate_64cube(G, use_graph):
+    """64^3 (the persistent kernel's 3D path) against the oracle for 8 iterations."""
+    n, L = (64, 64, 64), (8.0, 8.0, 8.0)
+    V = I.harmonic(n, L, [1.0, 1.0, 2.0])
+    eta, om = 500.0, 0.6
+    po = O.Problem(n, L, eta, om, V)
+    m = I.mesh(n, L)
+    phi0 = I.perturbed(I.normalise(I.anisotropic_gaussian(n, L, [1.0, 1.0, 2.0]) * (0.4 + 0.6 * (m[0] + 1j * m[1])), n, L), 9, n, L)
+    K = 8
+    _, orep = O.pcg_solve(po, phi0, O.SolveOptions(max_iter=K), keep_iterates=(K,))
+    with make(n, L, eta, om, V, 0, G) as ctx:
+        phi = dev(phi0)
+        o = G.solve_opts_default()
+        o.max_iter = K
+        o.use_graph = use_graph
+        rep = ctx.pcg_solve(phi, o, log_cap=16)
+        assert rep["loop_kind"] == use_graph, rep["note"]
+    for n_ in range(K + 1):
+        assert abs(rep["log"][n_, 2] - orep["log"][n_]["E"]) <= 1e-12 * abs(orep["log"][n_]["E"])
+    assert phase_aligned_rel_l2(host(phi), orep["iterates"][K]) < 1e-9
+
+
+def test_pcg_mixed_loop_styles_agree(G):
+    """The persistent kernel and the graph loop run the same algorithm (their
+    reductions sum in different fixed orders): both reach the same ground state."""
+    w, po = _workload_problem("c64_2d")
+    res = {}
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 1, G) as ctx:
+        for ug in (2, 1):
+            phi = dev(w["phi0"])
+            o = G.solve_opts_default()
+            o.use_graph = ug
+            res[ug] = ctx.pcg_solve(phi, o, check=True)
+            assert res[ug]["loop_kind"] == ug, res[ug]["note"]
+    assert res[2]["res_inf"] < 1e-8 and res[1]["res_inf"] < 1e-8
+    assert abs(res[2]["E"] - res[1]["E"]) <= 1e-10 * abs(res[1]["E"])
+    assert res[2]["iters_lo"] > 0 and res[1]["iters_lo"] > 0
+
+
 def test_pcg_host_buffers_and_restart_from_solution(G):
     w, po = _workload_problem("c64_2d")
     with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 0, G) as ctx:
@@ -281,6 +322,7 @@ def test_full_size_mixed_solve_verified_by_oracle(G, name):
         phi = dev(w["phi0"])
         rep = ctx.pcg_solve(phi, check=True)
     assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
+    assert rep["loop_kind"] == 2, rep["note"]  # the configuration bench.py times
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
     assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
