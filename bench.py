@@ -6,9 +6,10 @@ vortex initial guess, mixed precision: complex64 phase then complex128
 refinement, stop at ||H phi - lambda phi||_inf < 1e-8), through the C ABI with
 phi already in device memory.  Alongside it the line reports:
 
-  roofline      H phi (the x and y passes of gpe_apply_H, complex64 + f32 V)
-                on a 256x256x512 grid (working set > L2), achieved = 20 B/pt
-                algorithmic bytes / CUDA-event time, vs the measured HBM peak;
+  roofline      H phi on a batch of 512 fields of 256x256 complex64 (gpe_apply_H_batch,
+                one thread-block cluster per field; 268 MB in + 268 MB out > L2),
+                achieved = algorithmic bytes (16 B/point + V once) / CUDA-event
+                time, vs the measured HBM peak;
   e2e           the same solve with phi in pinned HOST memory (H2D/D2H copies
                 inside the call and inside the timed region);
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload;
@@ -35,8 +36,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "fast256_2d"
 METRIC = "ground states/sec to residual 1e-8 (256², 128³); H·φ GB/s vs HBM peak"
 UNIT = "ground_states/s"
-HPHI_GRID = (256, 256, 512)
-HPHI_BYTES_PER_PT = 20  # read phi (c64) + V (f32), write H phi (c64)
+HPHI_BATCH = 512  # fields of 256x256 complex64 in the H phi roofline batch (268 MB in, 268 MB out)
 
 
 def parse():
@@ -250,29 +250,28 @@ def main():
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
 
-    # ---------------- roofline: H phi on a grid larger than L2 ----------------
-    hn = HPHI_GRID
-    HN = int(np.prod(hn))
-    hL = (8.0, 8.0, 8.0)
-    Vh = torch.zeros(HN, dtype=torch.float64, device=dev)
-    hctx = gpe.Context(hn, hL, 100.0, 0.5, Vh, prec=gpe.GPE_MIXED)
-    del Vh
+    # ---------------- roofline: H phi on a batch of fields larger than L2 ----------------
+    # HPHI_BATCH fields of the workload's grid, one thread-block cluster per field
+    # (gpe_apply_H_batch), complex64: algorithmic bytes = read phi + write H phi
+    # per point (16 B) + V once (4 B per grid point, shared by the batch).
+    NB = HPHI_BATCH
     g = torch.Generator(device=dev).manual_seed(1)
-    hphi = torch.randn(HN, dtype=torch.complex64, device=dev, generator=g)
+    hphi = torch.randn(NB * N, dtype=torch.complex64, device=dev, generator=g)
     hout = torch.empty_like(hphi)
     for _ in range(3):
-        hctx.apply_H(hphi, hphi, hout)
+        ctx.apply_H_batch(NB, hphi, hphi, hout)
     torch.cuda.synchronize()
     hms = []
     for _ in range(20):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        hctx.apply_H(hphi, hphi, hout)
+        ctx.apply_H_batch(NB, hphi, hphi, hout)
         b.record(stream)
         b.synchronize()
         hms.append(a.elapsed_time(b))
     h_ms = statistics.median(hms)
-    achieved = HPHI_BYTES_PER_PT * HN / (h_ms * 1e-3) / 1e9
+    hbytes = 16 * NB * N + 4 * N
+    achieved = hbytes / (h_ms * 1e-3) / 1e9
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -280,7 +279,6 @@ def main():
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    hctx.close()
     del hphi, hout
 
     # ---------------- secondary: the 128^3 workload ----------------
@@ -325,12 +323,13 @@ def main():
                        "omega": 0.9, "V": "r^2/2", "precision": "mixed (c64 phase, c128 refinement)",
                        "tol_res_inf": 1e-8, "iters": last["iters"], "iters_c64": last["iters_lo"],
                        "loop": {2: "persistent kernel", 1: "graph", 0: "host loop"}[last["loop_kind"]],
+                       "loop_note": last.get("note", ""),
                        "E": last["E"], "res_inf": last["res_inf"],
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "H phi = pass_x<HX> + pass_s<HMID> (y, z) of gpe_apply_H, complex64",
-                         "grid": "x".join(map(str, hn)), "bytes_per_launch": HPHI_BYTES_PER_PT * HN,
+                         "kernel": "cluster_apply_H<float,256> (gpe_apply_H_batch: one 16-CTA cluster per field)",
+                         "grid": f"{NB} x 256x256", "bytes_per_launch": hbytes,
                          "ms_per_launch": h_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
             "gpu_launches": launches,

@@ -75,7 +75,7 @@ typedef struct {
   int max_backtracks;   /* trial step halvings before a step is taken anyway [30] */
   int cg;               /* 1: Algorithm 2 (PCG), 0: Algorithm 1 (PG) [1] */
   /* GPE_MIXED only: the complex64 phase ends, and the complex128 phase
-   * restarts the conjugate directions (beta = 0), when ||r||_inf falls below
+   * starts (see refine_restart), when ||r||_inf falls below
    * switch_res, or -- switch_res <= 0 -- below 4x an estimate of the
    * single-precision floor, eps32 (max_k |k|^2/2 + max V + |lambda|) max|phi|;
    * or when ||r||_inf has not halved within stall_window iterations while
@@ -83,11 +83,15 @@ typedef struct {
   int stall_window;     /* [500] */
   double switch_res;    /* [0: automatic] */
   int max_iter_lo;      /* cap on complex64-phase iterations [max_iter] */
-  int use_graph;        /* how the iteration loop runs [2]:
-                         * 2: one persistent cooperative kernel for the whole loop (square 2D grids with
-                         *    n in [64,512], cubic 3D grids with n in [64,256]; others fall back to 1);
+  int use_graph;        /* how the iteration loop runs [1]:
                          * 1: one CUDA graph launch whose WHILE node repeats the per-pass kernels;
+                         * 2: one persistent cooperative kernel for the whole loop, its passes separated
+                         *    by grid barriers (square 2D grids with n in [64,512], cubic 3D grids with
+                         *    n in [64,256]; others fall back to 1);
                          * 0: the per-pass kernels launched from a host loop. */
+  int refine_restart;   /* GPE_MIXED: 1 restarts the conjugate directions (beta = 0, p = 0) when the
+                         * complex128 phase starts; 0 carries the last complex64 direction p_{n-1},
+                         * r_{n-1} and <r_{n-1}, P r_{n-1}> over [1] */
 } gpe_solve_opts;
 
 /* Per-iteration log row, doubles: */
@@ -135,6 +139,17 @@ gpe_status gpe_destroy(gpe_ctx* ctx);
  * out_dev: device fields in working precision; out may alias f but not phi.
  * Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
 gpe_status gpe_apply_H(gpe_ctx* ctx, const void* phi_dev, const void* f_dev, void* out_dev);
+
+/* out_b = H_{phi_b} f_b for b = 0 .. nbatch-1 (the operator of gpe_apply_H,
+ * Section 2 / eq. FFTdiscret), on nbatch fields stored one after another
+ * (stride nx*ny elements), all with the context's V, eta and omega.  2D
+ * contexts with nx == ny in [32, 256] only.  Each field is transformed by one
+ * thread-block cluster entirely in distributed shared memory, so global
+ * memory is read and written once per point.  phi_dev, f_dev, out_dev: device
+ * arrays in working precision; f may equal phi; out must not overlap phi or
+ * f.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other grids),
+ * GPE_ERR_CUDA. */
+gpe_status gpe_apply_H_batch(gpe_ctx* ctx, int nbatch, const void* phi_dev, const void* f_dev, void* out_dev);
 
 /* out = P_C r = P_V^{1/2} P_Delta P_V^{1/2} r (eq. combinedP_12) with
  * P_Delta = (alpha - Delta/2)^{-1} (eq. PDelta) and

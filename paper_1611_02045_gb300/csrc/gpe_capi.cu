@@ -14,6 +14,7 @@
 #include "../../include/gpe.h"
 #include "gpe_internal.h"
 #include "gpe_persist.cuh"
+#include "gpe_cluster.cuh"
 
 using namespace gpe;
 
@@ -238,7 +239,8 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->stall_window = 500;
   o->switch_res = 0.0;
   o->max_iter_lo = 0;
-  o->use_graph = 2;
+  o->use_graph = 1;
+  o->refine_restart = 1;
   return GPE_OK;
 }
 
@@ -350,6 +352,26 @@ extern "C" gpe_status gpe_apply_H(gpe_ctx* c, const void* phi, const void* f, vo
   if (!c) return GPE_ERR_ARG;
   if (!phi || !f || !out) { c->err = "null field pointer"; return GPE_ERR_ARG; }
   return run_H(c, c->work, phi, f, out, c->ctl_api);
+}
+
+extern "C" gpe_status gpe_apply_H_batch(gpe_ctx* c, int nbatch, const void* phi, const void* f, void* out) {
+  if (!c) return GPE_ERR_ARG;
+  if (nbatch < 0 || !phi || !f || !out) { c->err = "bad batch arguments"; return GPE_ERR_ARG; }
+  if (c->dim != 2 || c->n[0] != c->n[1] || c->n[0] < 32 || c->n[0] > 256) {
+    c->err = "gpe_apply_H_batch needs a 2D grid with nx == ny in [32, 256]";
+    return GPE_ERR_UNSUPPORTED;
+  }
+  if (nbatch == 0) return GPE_OK;
+  const int prec = c->work;
+  const PrecBufs& b = c->pb[prec];
+  ClusterHArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.M = c->n[0]; a.nbatch = nbatch; a.stride = c->N;
+  a.eta = c->prob.eta; a.omega = c->prob.omega;
+  a.xi = b.xi[0]; a.xiy = b.xi[1]; a.xc = b.xc[0]; a.yc = b.xc[1]; a.tw = b.tw[0]; a.V = b.V;
+  a.phi = phi; a.f = f; a.out = out;
+  GPE_CU(c, launch_cluster_apply_H(prec, a, c->st));
+  return GPE_OK;
 }
 
 extern "C" gpe_status gpe_energy(gpe_ctx* c, const void* phi, double out[8]) {
@@ -585,14 +607,16 @@ static gpe_status warm_kernels(gpe_ctx* c, int mode) {
   return GPE_OK;
 }
 
-static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& o) {
+static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& o, bool keep_direction = false) {
   const IterBufs b = iter_bufs(c, mode);
   const size_t sbytes = (b.tab_h ? 16 : 8) * (size_t)c->N;
   const size_t dbytes = (b.tab_d ? 16 : 8) * (size_t)c->N;
   gpe_status s = warm_kernels(c, mode);
   if (s != GPE_OK) return s;
-  GPE_CU(c, cudaMemsetAsync(b.p, 0, dbytes, c->st));
-  GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, sbytes, c->st));
+  if (!keep_direction) {
+    GPE_CU(c, cudaMemsetAsync(b.p, 0, dbytes, c->st));
+    GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, sbytes, c->st));
+  }
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
   GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->st));
   bool done_launch = false;
@@ -678,9 +702,16 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
       GPE_CU(c, launch_convert_c64_to_c128(c->pb[0].phi, c->pb[1].phi, c->N, c->st));
     }
     if (go_on && h.iter < o.max_iter) {
-      h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = 1; h.stop_dE = 0;
+      const bool keep = !o.refine_restart;
+      h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = keep ? 0 : 1;
+      h.stop_dE = 0;
       h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter;
-      s = run_phase(c, 2, h, o);  // refinement: FP64 state, FP32 direction
+      if (keep) {
+        // the refinement reads p (complex64, shared with the first phase) and
+        // r_{n-1} in FP64: widen the first phase's r_{n-1}
+        GPE_CU(c, launch_convert_c64_to_c128(c->pb[0].r_prev, c->pb[1].r_prev, c->N, c->st));
+      }
+      s = run_phase(c, 2, h, o, keep);  // refinement: FP64 state, FP32 direction
       if (s != GPE_OK) return s;
     }
   } else {

@@ -1,0 +1,25 @@
+// gpe_cluster.cu -- instantiations and dispatch of the cluster H phi kernel.
+#include "gpe_cluster.cuh"
+
+namespace gpe {
+
+cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStream_t st) {
+  if (is_double) {
+    switch (a.M) {
+      case 32: return launch_cluster_apply_H_one<double, 32>(a, st);
+      case 64: return launch_cluster_apply_H_one<double, 64>(a, st);
+      case 128: return launch_cluster_apply_H_one<double, 128>(a, st);
+      case 256: return launch_cluster_apply_H_one<double, 256>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (a.M) {
+    case 32: return launch_cluster_apply_H_one<float, 32>(a, st);
+    case 64: return launch_cluster_apply_H_one<float, 64>(a, st);
+    case 128: return launch_cluster_apply_H_one<float, 128>(a, st);
+    case 256: return launch_cluster_apply_H_one<float, 256>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gpe

@@ -117,6 +117,11 @@ cudaError_t launch_group_f64_c(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_a(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_split(Pass pass, const PassArgs& a, cudaStream_t st);
 
+// H phi on a batch of 2D fields, one thread-block cluster per field
+// (gpe_cluster.cu); args is a ClusterHArgs (gpe_cluster.cuh).
+struct ClusterHArgs;
+cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStream_t st);
+
 // Small elementwise/control kernels (gpe_misc.cu).
 cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st);
 cudaError_t launch_convert_c64_to_c128(const void* src, void* dst, long long n, cudaStream_t st);

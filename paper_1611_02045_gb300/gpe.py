@@ -35,7 +35,7 @@ class gpe_solve_opts(C.Structure):
     _fields_ = [("tol_res_inf", C.c_double), ("tol_dE", C.c_double), ("max_iter", C.c_int),
                 ("theta_default", C.c_double), ("max_backtracks", C.c_int), ("cg", C.c_int),
                 ("stall_window", C.c_int), ("switch_res", C.c_double), ("max_iter_lo", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("refine_restart", C.c_int)]
 
 
 class gpe_report(C.Structure):
@@ -52,7 +52,7 @@ class GpeError(RuntimeError):
 
 
 _lib = None
-EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_precond",
+EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_apply_H_batch", "gpe_precond",
             "gpe_energy", "gpe_pcg_solve", "gpe_last_error")
 
 
@@ -68,6 +68,7 @@ def lib():
         L.gpe_create.argtypes = [C.POINTER(gpe_problem), vp, vp, C.POINTER(vp)]
         L.gpe_destroy.argtypes = [vp]
         L.gpe_apply_H.argtypes = [vp, vp, vp, vp]
+        L.gpe_apply_H_batch.argtypes = [vp, C.c_int, vp, vp, vp]
         L.gpe_precond.argtypes = [vp, vp, vp, C.c_double, vp]
         L.gpe_energy.argtypes = [vp, vp, C.POINTER(C.c_double)]
         L.gpe_pcg_solve.argtypes = [vp, vp, C.POINTER(gpe_solve_opts), C.POINTER(gpe_report)]
@@ -133,6 +134,9 @@ class Context:
 
     def apply_H(self, phi, f, out):
         return self._check(lib().gpe_apply_H(self._ctx, _addr(phi), _addr(f), _addr(out)))
+
+    def apply_H_batch(self, nbatch, phi, f, out):
+        return self._check(lib().gpe_apply_H_batch(self._ctx, int(nbatch), _addr(phi), _addr(f), _addr(out)))
 
     def precond(self, phi, r, alpha, out):
         return self._check(lib().gpe_precond(self._ctx, _addr(phi), _addr(r), float(alpha), _addr(out)))

@@ -88,6 +88,45 @@ def test_apply_H_matches_oracle(G, n, L, prec):
         assert relmax(got, want) < tol, (smooth, relmax(got, want))
 
 
+@pytest.mark.parametrize("M", [32, 64, 128, 256])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_apply_H_batch_cluster_matches_oracle(G, M, prec):
+    """gpe_apply_H_batch (one thread-block cluster per field, fields in
+    distributed shared memory) against the oracle, field by field, for f = phi
+    and f != phi, and against gpe_apply_H."""
+    n, L = (M, M), (7.0, 5.0)
+    V = I.harmonic(n, L)
+    eta, om = 29.0, 0.6
+    po = O.Problem(n, L, eta, om, V)
+    nb = 3
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    phis = np.stack([I.random_field(10 + b, n, L) for b in range(nb)])
+    fs = np.stack([I.random_field(20 + b, n, L) for b in range(nb)])
+    phi_d, f_d = dev(phis, dt), dev(fs, dt)
+    tol = 1e-12 if prec == 0 else 2e-5
+    with make(n, L, eta, om, V, prec, G) as ctx:
+        for same in (True, False):
+            out = torch.full_like(phi_d, float("nan"))
+            ctx.apply_H_batch(nb, phi_d, phi_d if same else f_d, out)
+            got = host(out)
+            ph, ff = host(phi_d), host(phi_d if same else f_d)
+            for b in range(nb):
+                want = O.apply_H(po, ph[b], ff[b])
+                assert relmax(got[b], want) < tol, (same, b, relmax(got[b], want))
+                one = torch.empty_like(phi_d[b])
+                ctx.apply_H(phi_d[b], (phi_d if same else f_d)[b], one)
+                assert relmax(got[b], host(one)) < tol
+
+
+def test_apply_H_batch_rejects_unsupported_grids(G):
+    n, L = (64, 32), (4.0, 4.0)
+    with make(n, L, 1.0, 0.0, I.harmonic(n, L), 0, G) as ctx:
+        x = dev(np.zeros((32, 64)))
+        with pytest.raises(G.GpeError) as e:
+            ctx.apply_H_batch(1, x, x, x)
+        assert e.value.status == G.GPE_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("n,L", GRIDS[:7])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_precond_matches_oracle(G, n, L, prec):
@@ -263,7 +302,8 @@ def test_pcg_3d_per_iterate_64cube(G, use_graph):
     assert phase_aligned_rel_l2(host(phi), orep["iterates"][K]) < 1e-9
 
 
-def test_pcg_mixed_loop_styles_agree(G):
+@pytest.mark.parametrize("refine_restart", [1, 0])
+def test_pcg_mixed_loop_styles_agree(G, refine_restart):
     """The persistent kernel and the graph loop run the same algorithm (their
     reductions sum in different fixed orders): both reach the same ground state."""
     w, po = _workload_problem("c64_2d")
@@ -273,6 +313,7 @@ def test_pcg_mixed_loop_styles_agree(G):
             phi = dev(w["phi0"])
             o = G.solve_opts_default()
             o.use_graph = ug
+            o.refine_restart = refine_restart
             res[ug] = ctx.pcg_solve(phi, o, check=True)
             assert res[ug]["loop_kind"] == ug, res[ug]["note"]
     assert res[2]["res_inf"] < 1e-8 and res[1]["res_inf"] < 1e-8
@@ -322,7 +363,7 @@ def test_full_size_mixed_solve_verified_by_oracle(G, name):
         phi = dev(w["phi0"])
         rep = ctx.pcg_solve(phi, check=True)
     assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
-    assert rep["loop_kind"] == 2, rep["note"]  # the configuration bench.py times
+    assert rep["loop_kind"] == G.solve_opts_default().use_graph, rep["note"]  # the loop bench.py times
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
     assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
