@@ -230,7 +230,10 @@ def main():
     launches = 0
     for r in reps:
         it, lo = r["iters"], r["iters_lo"]
-        if r["loop_kind"] == 2:
+        if r["loop_kind"] == 3:
+            # conversions (2), normalisations (2), one cluster kernel for the complex64 phase, then the graph
+            launches += 2 + 2 + 1 + 7 * (it - lo + 1)
+        elif r["loop_kind"] == 2:
             # two precision conversions; per phase one normalisation kernel and one persistent solve kernel
             launches += 2 + 2 + 2
         else:
@@ -322,7 +325,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": "256x256", "domain": "[-16,16]^2", "eta": 1000.0,
                        "omega": 0.9, "V": "r^2/2", "precision": "mixed (c64 phase, c128 refinement)",
                        "tol_res_inf": 1e-8, "iters": last["iters"], "iters_c64": last["iters_lo"],
-                       "loop": {2: "persistent kernel", 1: "graph", 0: "host loop"}[last["loop_kind"]],
+                       "loop": {3: "cluster (complex64 phase) + graph (refinement)", 2: "persistent kernel",
+                                1: "graph", 0: "host loop"}[last["loop_kind"]],
                        "loop_note": last.get("note", ""),
                        "E": last["E"], "res_inf": last["res_inf"],
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},

@@ -83,7 +83,10 @@ typedef struct {
   int stall_window;     /* [500] */
   double switch_res;    /* [0: automatic] */
   int max_iter_lo;      /* cap on complex64-phase iterations [max_iter] */
-  int use_graph;        /* how the iteration loop runs [1]:
+  int use_graph;        /* how the iteration loop runs [3]:
+                         * 3: GPE_MIXED 2D grids with nx == ny in [32, 256]: the complex64 phase runs in one
+                         *    thread-block cluster with every field in distributed shared memory; other
+                         *    phases and grids use 1;
                          * 1: one CUDA graph launch whose WHILE node repeats the per-pass kernels;
                          * 2: one persistent cooperative kernel for the whole loop, its passes separated
                          *    by grid barriers (square 2D grids with n in [64,512], cubic 3D grids with
@@ -114,7 +117,8 @@ typedef struct {
   int log_cap;       /* in: rows available in log (0: no log) */
   int log_len;       /* out: rows written (min(iters + 1, log_cap)) */
   double* log;       /* in: host array [log_cap][GPE_LOG_FIELDS] or NULL */
-  int loop_kind;     /* out: loop style of the last phase: 2 persistent kernel, 1 graph, 0 host loop */
+  int loop_kind;     /* out: loop style that ran (for GPE_MIXED: of the complex64 phase):
+                      * 3 cluster, 2 persistent, 1 graph, 0 host loop */
 } gpe_report;
 
 typedef struct gpe_ctx gpe_ctx;

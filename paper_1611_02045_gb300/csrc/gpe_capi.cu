@@ -15,6 +15,7 @@
 #include "gpe_internal.h"
 #include "gpe_persist.cuh"
 #include "gpe_cluster.cuh"
+#include "gpe_csolve.cuh"
 
 using namespace gpe;
 
@@ -239,7 +240,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->stall_window = 500;
   o->switch_res = 0.0;
   o->max_iter_lo = 0;
-  o->use_graph = 1;
+  o->use_graph = 3;
   o->refine_restart = 1;
   return GPE_OK;
 }
@@ -620,11 +621,30 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
   GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->st));
   bool done_launch = false;
-  if (o.use_graph == 2 && persist_eligible(c)) {
+  int loop = o.use_graph ? 1 : 0;
+  if (o.use_graph == 3 && mode == 0 && c->dim == 2 && c->n[0] == c->n[1] && c->n[0] >= 32 && c->n[0] <= 256) {
+    // the complex64 phase held in one thread-block cluster's shared memory
+    ClusterSolveArgs P;
+    std::memset(&P, 0, sizeof(P));
+    P.base = iter_args(c, 0, 0ull).hx;
+    P.phi = static_cast<float2*>(b.phi);
+    P.V = static_cast<const float*>(b.V);
+    P.ctl = c->ctl_solve;
+    cudaError_t e = launch_cluster_solve(c->n[0], P, c->st);
+    if (e == cudaSuccess) {
+      done_launch = true;
+      loop = 3;
+    } else {
+      cudaGetLastError();
+      c->err = std::string("cluster solve unavailable, graph loop used: ") + cudaGetErrorString(e);
+    }
+  }
+  if (!done_launch && o.use_graph == 2 && persist_eligible(c)) {
     s = run_persistent(c, mode, &done_launch);
     if (s != GPE_OK) return s;
+    if (done_launch) loop = 2;
   }
-  c->last_loop = done_launch ? 2 : (o.use_graph ? 1 : 0);
+  if (mode != 2) c->last_loop = loop;  // a mixed solve reports its complex64 phase's loop
   if (done_launch) {
   } else if (o.use_graph) {
     s = build_graph(c, mode);
@@ -698,7 +718,9 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
     const bool go_on = h.switch_req || h.status == 0;  // a complex64 "success" is refined too
     if (h.status == GPE_ERR_NONFINITE || h.status == GPE_ERR_PRECOND) {
       // keep the input in the complex128 buffer; report the failure
-    } else if (go_on) {
+    } else {
+      // the last complex64 iterate: the refinement's start, or the answer when
+      // the iteration cap ended the solve in the complex64 phase
       GPE_CU(c, launch_convert_c64_to_c128(c->pb[0].phi, c->pb[1].phi, c->N, c->st));
     }
     if (go_on && h.iter < o.max_iter) {

@@ -1,5 +1,6 @@
 // gpe_cluster.cu -- instantiations and dispatch of the cluster H phi kernel.
 #include "gpe_cluster.cuh"
+#include "gpe_csolve.cuh"
 
 namespace gpe {
 
@@ -18,6 +19,16 @@ cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStr
     case 64: return launch_cluster_apply_H_one<float, 64>(a, st);
     case 128: return launch_cluster_apply_H_one<float, 128>(a, st);
     case 256: return launch_cluster_apply_H_one<float, 256>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_cluster_solve(int M, const ClusterSolveArgs& P, cudaStream_t st) {
+  switch (M) {
+    case 32: return launch_cluster_solve_one<32>(P, st);
+    case 64: return launch_cluster_solve_one<64>(P, st);
+    case 128: return launch_cluster_solve_one<128>(P, st);
+    case 256: return launch_cluster_solve_one<256>(P, st);
     default: return cudaErrorInvalidValue;
   }
 }

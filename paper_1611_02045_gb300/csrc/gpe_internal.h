@@ -72,6 +72,7 @@ struct PassArgs {
   int axis;        // physical axis transformed by this pass
   int M;           // length along that axis
   int lpb;         // contiguous passes: lines per block
+  int row0;        // contiguous passes: global row of line 0 (field slices held by one CTA)
   int tx;          // strided passes: tile width in x
   long long stride;        // strided: element stride along the axis
   long long outer_stride;  // strided: element stride of the outer index
@@ -121,6 +122,11 @@ cudaError_t launch_group_split(Pass pass, const PassArgs& a, cudaStream_t st);
 // (gpe_cluster.cu); args is a ClusterHArgs (gpe_cluster.cuh).
 struct ClusterHArgs;
 cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStream_t st);
+
+// The complex64 phase of a 2D solve in one thread-block cluster's shared
+// memory (gpe_csolve.cuh; M = nx = ny in [32, 256]).
+struct ClusterSolveArgs;
+cudaError_t launch_cluster_solve(int M, const ClusterSolveArgs& P, cudaStream_t st);
 
 // Small elementwise/control kernels (gpe_misc.cu).
 cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st);

@@ -85,7 +85,20 @@ __device__ __forceinline__ Acc shfl_acc(unsigned mask, Acc v, int o) {
   return Acc{__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o)};
 }
 
-// Block total of v[k] (fixed tree); valid in thread 0 on return.
+// Fixed-order butterfly over the 32 lanes of a warp (lanes beyond the data
+// hold the identity, 0, which also serves the max slots: they are >= 0).
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ void warp_tree(Acc (&v)[K]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = red_op<MAXMASK>(v[k], shfl_acc(0xffffffffu, v[k], o), k);
+  }
+}
+
+// Block total of v[k] (fixed tree); valid in thread 0 on return.  Warp sums
+// by shuffles, then warp 0 combines the per-warp sums with a second shuffle
+// tree (no serial loop over warps).
 template <int K, unsigned MAXMASK>
 __device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
   // blockDim.x is a power of two: either a multiple of 32 or one partial warp
@@ -93,22 +106,23 @@ __device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
   const int width = blockDim.x < 32 ? (int)blockDim.x : 32;
   const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    for (int o = width >> 1; o > 0; o >>= 1) v[k] = red_op<MAXMASK>(v[k], shfl_acc(mask, v[k], o), k);
+  for (int o = 16; o > 0; o >>= 1) {
+    if (o < width) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = red_op<MAXMASK>(v[k], shfl_acc(mask, v[k], o), k);
+    }
   }
+  if (nw == 1) return;
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) red_sm[warp * K + k] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      Acc a = red_sm[k];
-      for (int w = 1; w < nw; ++w) a = red_op<MAXMASK>(a, red_sm[w * K + k], k);
-      v[k] = a;
-    }
+    for (int k = 0; k < K; ++k) v[k] = lane < nw ? red_sm[lane * K + k] : Acc{0.0f, 0.0f};
+    warp_tree<K, MAXMASK>(v);
   }
 }
 
@@ -381,7 +395,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
   const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
   const long long line = unit * a.lpb + l;
   const long long base = line * M;
-  const int iy = (int)(line % a.ny);
+  const int iy = (int)((a.row0 + line) % a.ny);  // row0: global row of local line 0 (cluster slices)
   const CF* __restrict__ tw = static_cast<const CF*>(a.tw);
   const TF* __restrict__ xi = tab<TF>(a.xi[0]);
   const TS* __restrict__ V = tab<TS>(a.V);

@@ -68,7 +68,7 @@ int main(void) {
 def test_solve_opts_defaults(built_lib):
     o = G.solve_opts_default()
     assert o.tol_res_inf == 1e-8 and o.max_iter == 20000 and o.theta_default == 0.1
-    assert o.max_backtracks == 30 and o.cg == 1 and o.use_graph == 1 and o.refine_restart == 1
+    assert o.max_backtracks == 30 and o.cg == 1 and o.use_graph == 3 and o.refine_restart == 1
     assert G.lib().gpe_solve_opts_default(None) == G.GPE_ERR_ARG
 
 

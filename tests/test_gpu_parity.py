@@ -321,6 +321,54 @@ def test_pcg_mixed_loop_styles_agree(G, refine_restart):
     assert res[2]["iters_lo"] > 0 and res[1]["iters_lo"] > 0
 
 
+@pytest.mark.parametrize("name", ["c64_2d", "fast256_2d"])
+def test_cluster_complex64_phase_iterates(G, name):
+    """use_graph = 3: the complex64 phase in one thread-block cluster's shared
+    memory.  Its first 15 iterates against the FP64 oracle at complex64
+    tolerance (E_n rel 2e-6, phi_n phase-aligned L2 2e-4), and against the same
+    phase run by the graph loop."""
+    w, po = _workload_problem(name)
+    K = 15
+    _, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions(max_iter=K), keep_iterates=(K,))
+    logs, phis = {}, {}
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 1, G) as ctx:
+        for ug in (3, 1):
+            phi = dev(w["phi0"])
+            o = G.solve_opts_default()
+            o.use_graph = ug
+            o.max_iter = K
+            o.switch_res = 1e-30
+            o.stall_window = 1 << 30
+            rep = ctx.pcg_solve(phi, o, log_cap=32)
+            assert rep["loop_kind"] == ug, rep["note"]
+            assert rep["iters"] == K and rep["iters_lo"] == K
+            logs[ug], phis[ug] = rep["log"], host(phi)
+    for n_ in range(K + 1):
+        e = orep["log"][n_]["E"]
+        assert abs(logs[3][n_, 2] - e) <= 2e-6 * abs(e), n_
+        assert abs(logs[3][n_, 2] - logs[1][n_, 2]) <= 2e-6 * abs(e), n_
+    assert phase_aligned_rel_l2(phis[3], orep["iterates"][K]) < 2e-4
+    assert phase_aligned_rel_l2(phis[3], phis[1]) < 2e-4
+
+
+@pytest.mark.parametrize("name", ["c64_2d", "fast256_2d"])
+def test_cluster_mixed_solve_reaches_fp64_answer(G, name):
+    w, po = _workload_problem(name)
+    with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 1, G) as ctx:
+        phi = dev(w["phi0"])
+        o = G.solve_opts_default()
+        o.use_graph = 3
+        rep = ctx.pcg_solve(phi, o, check=True)
+        assert rep["loop_kind"] == 3, rep["note"]
+        ref = dev(w["phi0"])
+        rep1 = ctx.pcg_solve(ref, check=True)
+    assert rep["res_inf"] < 1e-8 and rep["iters_lo"] > 0
+    assert abs(rep["E"] - rep1["E"]) <= 1e-10 * abs(rep1["E"])
+    ph = host(phi)
+    r = O.apply_H(po, ph, ph) - O.chemical_potential(po, ph) * ph
+    assert np.max(np.abs(r)) < 1.05e-8
+
+
 def test_pcg_host_buffers_and_restart_from_solution(G):
     w, po = _workload_problem("c64_2d")
     with make(w["n"], w["L"], w["eta"], w["omega"], w["V"], 0, G) as ctx:
@@ -363,7 +411,8 @@ def test_full_size_mixed_solve_verified_by_oracle(G, name):
         phi = dev(w["phi0"])
         rep = ctx.pcg_solve(phi, check=True)
     assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
-    assert rep["loop_kind"] == G.solve_opts_default().use_graph, rep["note"]  # the loop bench.py times
+    want = 3 if len(w["n"]) == 2 else 1  # the loops bench.py times (cluster for 2D, graph for 3D)
+    assert rep["loop_kind"] == want, rep["note"]
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
     assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
