@@ -191,8 +191,9 @@ def main():
     phi_d = torch.empty_like(phi0_d)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    opts = gpe.solve_opts_default()
-    opts.use_graph = 0 if args.no_graph else 1
+    opts = gpe.solve_opts_default()  # the library's default loop for this grid
+    if args.no_graph:
+        opts.use_graph = 0
 
     def solve_dev():
         phi_d.copy_(phi0_d)

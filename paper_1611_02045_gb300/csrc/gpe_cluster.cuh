@@ -41,8 +41,11 @@ struct ClusterHArgs {
   void* out;         // results
 };
 
+// Two CTAs per SM in single precision (two fields in flight per SM group).
+template <typename T> struct ClusterMinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+
 template <typename T, int M>
-__global__ void __launch_bounds__((M / 8) * kClusterRows) cluster_apply_H(ClusterHArgs a) {
+__global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::value) cluster_apply_H(ClusterHArgs a) {
   using C = cplx<T>;
   constexpr int E = 8, Tl = M / 8, R = kClusterRows;
   constexpr int LS = M + M / 16;
@@ -68,20 +71,17 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows) cluster_apply_H(Cluste
     const C* __restrict__ phi = static_cast<const C*>(a.phi);
     const T* __restrict__ V = static_cast<const T*>(a.V);
     const bool same = (a.f == a.phi);
-    C v[E];
+    C w[E];
     T m[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int x = t + q * Tl;
       const long long g = fb + (long long)y * M + x;
-      v[q] = f[g];
-      const C ph = same ? v[q] : phi[g];
+      w[q] = f[g];
+      const C ph = same ? w[q] : phi[g];
       m[q] = V[(long long)y * M + x] + T(a.eta) * (ph.x * ph.x + ph.y * ph.y);
-      fs[l * M + x] = v[q];
+      fs[l * M + x] = w[q];
     }
-    C w[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) w[q] = v[q];
     auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
     line_dft<M, E, -1>(w, xs, si, t, tw);
     const T yy = static_cast<const T*>(a.yc)[y];
@@ -92,7 +92,10 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows) cluster_apply_H(Cluste
     }
     line_dft<M, E, +1>(w, xs, si, t, tw);
 #pragma unroll
-    for (int q = 0; q < E; ++q) ts[l * M + t + q * Tl] = cmk<C>(w[q].x + m[q] * v[q].x, w[q].y + m[q] * v[q].y);
+    for (int q = 0; q < E; ++q) {
+      const C v = fs[l * M + t + q * Tl];  // the operand, kept in shared memory
+      ts[l * M + t + q * Tl] = cmk<C>(w[q].x + m[q] * v.x, w[q].y + m[q] * v.y);
+    }
   }
   cl.sync();  // every CTA's rows of f and t are complete and visible
 
