@@ -54,7 +54,7 @@ struct gpe_ctx {
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   std::string err;
-  PrecBufs pb[2];  // 0: float / complex64, 1: double / complex128
+  PrecBufs pb[3];  // 0: float / complex64, 1: double / complex128, 2: double-single (refinement state)
   int work = 1;    // precision of API calls
   Ctl* ctl_solve = nullptr;
   Ctl* ctl_api = nullptr;
@@ -65,7 +65,7 @@ struct gpe_ctx {
   PassPlan plan[3];  // per axis
   double vmax = 0.0;  // max V on the grid
   int max_threads[2] = {512, 256};
-  bool warmed[3] = {false, false, false};
+  bool warmed[3] = {false, false, false};  // per launch mode
   int nsm = 0;                      // streaming multiprocessors of the device
   double* pers_partials = nullptr;  // persistent solve: [2][grid][kMaxMoments]
   unsigned* pers_bar = nullptr;     // persistent solve: barrier words + error flag
@@ -159,7 +159,7 @@ struct IterBufs {
 static IterBufs iter_bufs(gpe_ctx* c, int mode) {
   IterBufs b;
   b.mode = mode;
-  const int sp = mode == 0 ? 0 : 1;  // state precision
+  const int sp = mode == 0 ? 0 : (mode == 2 ? 2 : 1);  // state precision (2: double-single)
   const int dp = mode == 1 ? 1 : 0;  // direction precision
   b.tab_h = sp;
   b.tab_d = dp;
@@ -195,9 +195,10 @@ static cudaError_t upload_tables(gpe_ctx* c, PrecBufs& b) {
 static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
   PrecBufs& b = c->pb[prec];
   b.on = true;
-  const size_t cb = prec ? 16 : 8;
+  const size_t cb = prec ? 16 : 8;  // complex64 8 B; complex128 and double-single 16 B
   const size_t bytes = cb * (size_t)c->N;
-  GPE_CU(c, prec ? upload_tables<double>(c, b) : upload_tables<float>(c, b));
+  if (prec == 2) GPE_CU(c, upload_tables<dsf>(c, b));
+  else GPE_CU(c, prec ? upload_tables<double>(c, b) : upload_tables<float>(c, b));
   GPE_CU(c, cudaMalloc(&b.phi, bytes));
   GPE_CU(c, cudaMalloc(&b.p, bytes));
   GPE_CU(c, cudaMalloc(&b.t, bytes));
@@ -205,7 +206,11 @@ static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
   GPE_CU(c, cudaMalloc(&b.r_prev, bytes));
   GPE_CU(c, cudaMemset(b.p, 0, bytes));
   GPE_CU(c, cudaMemset(b.r_prev, 0, bytes));
-  if (prec) {
+  if (prec == 2) {
+    GPE_CU(c, cudaMalloc(&b.V, 8 * (size_t)c->N));
+    GPE_CU(c, launch_d2ds(Vdev64, b.V, c->N, 0));
+    GPE_CU(c, cudaDeviceSynchronize());
+  } else if (prec == 1) {
     GPE_CU(c, cudaMalloc(&b.V, 8 * (size_t)c->N));
     GPE_CU(c, cudaMemcpy(b.V, Vdev64, 8 * (size_t)c->N, cudaMemcpyDeviceToDevice));
   } else {
@@ -292,6 +297,7 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
   }
   gpe_status s = alloc_prec(c, 1, V64);
   if (s == GPE_OK && prob->prec == GPE_MIXED) s = alloc_prec(c, 0, V64);
+  if (s == GPE_OK && prob->prec == GPE_MIXED) s = alloc_prec(c, 2, V64);
   cudaFree(V64);
   if (s != GPE_OK) return fail(s);
 
@@ -728,13 +734,14 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
       h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = keep ? 0 : 1;
       h.stop_dE = 0;
       h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter;
-      if (keep) {
-        // the refinement reads p (complex64, shared with the first phase) and
-        // r_{n-1} in FP64: widen the first phase's r_{n-1}
-        GPE_CU(c, launch_convert_c64_to_c128(c->pb[0].r_prev, c->pb[1].r_prev, c->N, c->st));
-      }
-      s = run_phase(c, 2, h, o, keep);  // refinement: FP64 state, FP32 direction
+      // the refinement state lives in double-single: phi (and, when the
+      // direction is kept, r_{n-1}; p is complex64 in both phases)
+      GPE_CU(c, launch_convert_c64_to_ds(c->pb[0].phi, c->pb[2].phi, c->N, c->st));
+      if (keep) GPE_CU(c, launch_convert_c64_to_ds(c->pb[0].r_prev, c->pb[2].r_prev, c->N, c->st));
+      s = run_phase(c, 2, h, o, keep);  // refinement: double-single state, FP32 direction
       if (s != GPE_OK) return s;
+      if (h.status != GPE_ERR_NONFINITE && h.status != GPE_ERR_PRECOND)
+        GPE_CU(c, launch_convert_ds_to_c128(c->pb[2].phi, c->pb[1].phi, c->N, c->st));
     }
   } else {
     h.lo_phase = 0; h.phase = 1; h.max_iter_phase = o.max_iter;

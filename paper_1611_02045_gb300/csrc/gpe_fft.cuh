@@ -17,11 +17,14 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "gpe_ds.cuh"
+
 namespace gpe {
 
 template <typename T> struct cvec;
 template <> struct cvec<float> { using type = float2; };
 template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<dsf> { using type = dsc; };
 template <typename T> using cplx = typename cvec<T>::type;
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
@@ -40,6 +43,11 @@ template <int DIR, typename C> __device__ __forceinline__ C ctw(C a, C w) {
   return DIR < 0 ? cmk<C>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x)
                  : cmk<C>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
 }
+
+// Twiddle loads through the read-only path where the type allows it.
+__device__ __forceinline__ float2 ld_tw(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dsc ld_tw(const dsc* p) { return *p; }
 
 // ---------------------------------------------------------------------------
 // Small DFTs on registers: y_m = sum_r x_r e^{DIR 2 pi i r m / R}
@@ -125,7 +133,7 @@ __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t
     if constexpr (NS > 1) {
       const int k = j % NS;
 #pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = ctw<DIR>(x[r], __ldg(&tw[(k * r) * (M / (NS * R))]));
+      for (int r = 1; r < R; ++r) x[r] = ctw<DIR>(x[r], ld_tw(&tw[(k * r) * (M / (NS * R))]));
     }
     dft_small<R, DIR>(x);
 #pragma unroll

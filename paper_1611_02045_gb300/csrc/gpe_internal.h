@@ -132,8 +132,12 @@ cudaError_t launch_cluster_solve(int M, const ClusterSolveArgs& P, cudaStream_t 
 cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, cudaStream_t st);
 cudaError_t launch_convert_c64_to_c128(const void* src, void* dst, long long n, cudaStream_t st);
 cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t st);
+cudaError_t launch_d2ds(const double* src, void* dst, long long n, cudaStream_t st);
+cudaError_t launch_convert_c64_to_ds(const void* src, void* dst, long long n, cudaStream_t st);
+cudaError_t launch_convert_ds_to_c128(const void* src, void* dst, long long n, cudaStream_t st);
 // ctl->c = 1, s = 0, inv_nrm = 1 / ||phi||, retract = 1 (weighted norm), so
 // that the next H pass normalises phi in place.
-cudaError_t launch_init_norm(int is_double, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st);
+// prec: 0 complex64, 1 complex128, 2 double-single.
+cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st);
 
 }  // namespace gpe

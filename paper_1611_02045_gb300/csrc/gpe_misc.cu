@@ -1,6 +1,7 @@
 // gpe_misc.cu -- pass dispatch and the small elementwise kernels around a
 // solve (precision conversion, initial normalisation).
 #include "gpe_internal.h"
+#include "gpe_ds.cuh"
 
 namespace gpe {
 
@@ -23,12 +24,10 @@ static cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st
 cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
   if (mode == 0) return launch_pass_f32(pass, a, st);
   if (mode == 1) return launch_pass_f64(pass, a, st);
-  // refinement split: H phi in FP64 (y/z passes are plain complex128), the
-  // contiguous direction passes mix precisions, the strided direction passes
-  // are plain complex64.
+  // refinement split: H phi and the state in double-single, the strided
+  // direction passes are plain complex64.
   switch (pass) {
-    case P_HX: case P_C1: case P_C3: case P_AX: return launch_group_split(pass, a, st);
-    case P_HMID: return launch_pass_f64(pass, a, st);
+    case P_HX: case P_HMID: case P_C1: case P_C3: case P_AX: return launch_group_split(pass, a, st);
     default: return launch_pass_f32(pass, a, st);
   }
 }
@@ -50,6 +49,23 @@ __global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, long 
     d[i] = (float)s[i];
 }
 
+// double-single <-> complex64 / complex128 (the refinement state)
+__global__ void k_c64_to_ds(const float2* __restrict__ s, dsc* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = s[i];
+    dsc o;
+    o.x = dsf(v.x);
+    o.y = dsf(v.y);
+    d[i] = o;
+  }
+}
+__global__ void k_ds_to_c128(const dsc* __restrict__ s, double2* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dsc v = s[i];
+    d[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
 static int grid_for(long long n) {
   long long g = (n + 255) / 256;
   return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
@@ -61,6 +77,22 @@ cudaError_t launch_convert_c128_to_c64(const void* src, void* dst, long long n, 
 }
 cudaError_t launch_convert_c64_to_c128(const void* src, void* dst, long long n, cudaStream_t st) {
   k_c64_to_c128<<<grid_for(n), 256, 0, st>>>((const float2*)src, (double2*)dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_c64_to_ds(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_c64_to_ds<<<grid_for(n), 256, 0, st>>>((const float2*)src, (dsc*)dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_ds_to_c128(const void* src, void* dst, long long n, cudaStream_t st) {
+  k_ds_to_c128<<<grid_for(n), 256, 0, st>>>((const dsc*)src, (double2*)dst, n);
+  return cudaGetLastError();
+}
+__global__ void k_d2ds(const double* __restrict__ s, dsf* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = dsf(s[i]);
+}
+cudaError_t launch_d2ds(const double* src, void* dst, long long n, cudaStream_t st) {
+  k_d2ds<<<grid_for(n), 256, 0, st>>>(src, (dsf*)dst, n);
   return cudaGetLastError();
 }
 cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t st) {
@@ -75,7 +107,8 @@ __global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, l
   double acc = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const C v = phi[i];
-    acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    const double re = (double)v.x, im = (double)v.y;
+    acc += re * re + im * im;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
@@ -91,8 +124,9 @@ __global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, l
   }
 }
 
-cudaError_t launch_init_norm(int is_double, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st) {
-  if (is_double) k_init_norm<double2><<<1, 1024, 0, st>>>((const double2*)phi, n, weight, ctl);
+cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st) {
+  if (prec == 1) k_init_norm<double2><<<1, 1024, 0, st>>>((const double2*)phi, n, weight, ctl);
+  else if (prec == 2) k_init_norm<dsc><<<1, 1024, 0, st>>>((const dsc*)phi, n, weight, ctl);
   else k_init_norm<float2><<<1, 1024, 0, st>>>((const float2*)phi, n, weight, ctl);
   return cudaGetLastError();
 }

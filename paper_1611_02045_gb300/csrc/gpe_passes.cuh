@@ -62,6 +62,7 @@ __device__ __forceinline__ Acc acc_from(double x) {
   const float h = (float)x;
   return Acc{h, (float)(x - (double)h)};
 }
+__device__ __forceinline__ Acc acc_from(dsf x) { return Acc{x.hi, x.lo}; }
 __device__ __forceinline__ double acc_to_double(Acc a) { return (double)a.hi + (double)a.lo; }
 
 __device__ __forceinline__ Acc acc_add(Acc a, Acc b) {
@@ -749,16 +750,17 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
 // ---------------------------------------------------------------------------
 // Host-side dispatch over M
 // ---------------------------------------------------------------------------
-// Precision modes of a launch: 0 complex64, 1 complex128, 2 refinement split
-// (state in FP64, direction in FP32; H passes transform in FP64).
+// Precision modes of a launch: 0 complex64, 1 complex128, 2 refinement split:
+// the state (phi, H phi, r_{n-1}, V) and the H phi transforms in double-single
+// (dsf, ~48 bits on the FP32 pipe), the direction (P_C workspace, p) in FP32.
 template <int MODE, int ROLE> struct ModeTypes;
 template <int ROLE> struct ModeTypes<0, ROLE> { using TF = float; using TS = float; using TD = float; };
 template <int ROLE> struct ModeTypes<1, ROLE> { using TF = double; using TS = double; using TD = double; };
 template <int ROLE> struct ModeTypes<2, ROLE> {
   static constexpr bool h = (ROLE == P_HX || ROLE == P_HMID);
   static constexpr bool state = (ROLE == P_C1 || ROLE == P_C3 || ROLE == P_AX);
-  using TF = typename std::conditional<h, double, float>::type;
-  using TS = typename std::conditional<h || state, double, float>::type;
+  using TF = typename std::conditional<h, dsf, float>::type;
+  using TS = typename std::conditional<h || state, dsf, float>::type;
   using TD = float;
 };
 
