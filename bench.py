@@ -37,6 +37,10 @@ WORKLOAD = "fast256_2d"
 METRIC = "ground states/sec to residual 1e-8 (256², 128³); H·φ GB/s vs HBM peak"
 UNIT = "ground_states/s"
 HPHI_BATCH = 512  # fields of 256x256 complex64 in the H phi roofline batch (268 MB in, 268 MB out)
+# DRAM bytes (read + write) of one cluster_apply_H<float,256> launch over HPHI_BATCH fields: an ncu
+# capture of a 256-field launch of the same kernel measured 134.5 MB + 91.4 MB; scaled by 512/256
+# fields (traffic grows in proportion to the fields).  Set to None when that kernel changes.
+HPHI_TRAFFIC_PER_LAUNCH = int(2 * (134.529536e6 + 91.378944e6))
 
 
 def parse():
@@ -332,7 +336,7 @@ def main():
                        "E": last["E"], "res_inf": last["res_inf"],
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": HPHI_TRAFFIC_PER_LAUNCH,
                          "kernel": "cluster_apply_H<float,256> (gpe_apply_H_batch: one 16-CTA cluster per field)",
                          "grid": f"{NB} x 256x256", "bytes_per_launch": hbytes,
                          "ms_per_launch": h_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},

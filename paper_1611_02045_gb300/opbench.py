@@ -20,12 +20,14 @@ def main():
     ap.add_argument("--grid", type=int, nargs="+", default=[256, 256, 512])
     ap.add_argument("--L", type=float, default=8.0)
     ap.add_argument("--prec", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--op", choices=["apply_H", "precond", "energy", "solve"], default="apply_H")
+    ap.add_argument("--op", choices=["apply_H", "apply_H_batch", "precond", "energy", "solve"], default="apply_H")
+    ap.add_argument("--batch", type=int, default=64, help="fields for --op apply_H_batch (2D grid)")
     ap.add_argument("--workload", default="fast256_2d", help="for --op solve")
     ap.add_argument("--max-iter", type=int, default=50, help="for --op solve")
     ap.add_argument("--switch-res", type=float, default=0.0, help="for --op solve (mixed)")
-    ap.add_argument("--loop", choices=["persistent", "graph", "host"], default="persistent",
-                    help="for --op solve: persistent kernel, graph with device-side loop, or host loop")
+    ap.add_argument("--loop", choices=["default", "cluster", "persistent", "graph", "host"], default="default",
+                    help="for --op solve: the library default, the cluster-resident complex64 phase, the "
+                         "persistent kernel, the graph with a device-side loop, or a host loop")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -46,7 +48,8 @@ def main():
         opts = gpe.solve_opts_default()
         opts.max_iter = a.max_iter
         opts.switch_res = a.switch_res
-        opts.use_graph = {"persistent": 2, "graph": 1, "host": 0}[a.loop]
+        if a.loop != "default":
+            opts.use_graph = {"cluster": 3, "persistent": 2, "graph": 1, "host": 0}[a.loop]
         times = []
         for i in range(a.warmup + a.iters):
             phi.copy_(phi0)
@@ -71,13 +74,17 @@ def main():
     del V
     dt = torch.complex128 if a.prec == "fp64" else torch.complex64
     g = torch.Generator(device=dev).manual_seed(1)
-    phi = torch.randn(N, dtype=dt, device=dev, generator=g)
+    nf = a.batch if a.op == "apply_H_batch" else 1
+    phi = torch.randn(N * nf, dtype=dt, device=dev, generator=g)
     out = torch.empty_like(phi)
     cb = 16 if a.prec == "fp64" else 8
     vb = 8 if a.prec == "fp64" else 4
     if a.op == "apply_H":
         call = lambda: ctx.apply_H(phi, phi, out)  # noqa: E731
         bytes_pt = 2 * cb + vb
+    elif a.op == "apply_H_batch":
+        call = lambda: ctx.apply_H_batch(nf, phi, phi, out)  # noqa: E731
+        bytes_pt = 2 * cb + vb / nf  # V is read once for the batch
     elif a.op == "precond":
         call = lambda: ctx.precond(phi, phi, 1.5, out)  # noqa: E731
         bytes_pt = 3 * cb + vb
@@ -96,9 +103,9 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
-    print(json.dumps({"op": a.op, "grid": list(n), "prec": a.prec, "points": N, "ms": ms,
+    print(json.dumps({"op": a.op, "grid": list(n), "fields": nf, "prec": a.prec, "points": N * nf, "ms": ms,
                       "algorithmic_bytes_per_point": bytes_pt,
-                      "effective_GBps": bytes_pt * N / (ms * 1e-3) / 1e9}))
+                      "effective_GBps": bytes_pt * N * nf / (ms * 1e-3) / 1e9}))
 
 
 if __name__ == "__main__":
