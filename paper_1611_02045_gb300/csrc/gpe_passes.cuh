@@ -410,6 +410,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
     const CS* __restrict__ f = static_cast<const CS*>(a.f ? a.f : a.phi);
     CS ph[E];
+    TS vv[E];
     const bool retract = S.retract;
     const TS cc = TS(retract ? S.c * S.inv_nrm : 1.0);
     const TS ss = TS(retract ? S.s * S.inv_np * S.inv_nrm : 0.0);
@@ -425,6 +426,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
         phi_out[g] = x;
       }
       ph[q] = x;
+      vv[q] = V[g];
       v[q] = cconv<TF>((a.f && !a.solver) ? f[g] : x);
     }
     line_dft<M, E, -1>(v, sm, si, t, tw);
@@ -446,12 +448,11 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const TS vv = V[g];
       const TS u = ph[q].x * ph[q].x + ph[q].y * ph[q].y;
-      const TS m = vv + eta * u;
+      const TS m = vv[q] + eta * u;
       const CS fq = (a.f && !a.solver) ? f[g] : ph[q];  // the operand f (re-read in API mode)
       tout[g] = cmk<CS>(TS(v[q].x) + m * fq.x, TS(v[q].y) + m * fq.y);
-      apot += vv * u; au2 += u * u; an2 += u; umax = fmax(umax, u);
+      apot += vv[q] * u; au2 += u * u; an2 += u; umax = fmax(umax, u);
     }
     acc[0] = acc_add(acc[0], acc_from(akin * invM));
     acc[1] = acc_add(acc[1], acc_from(arot * invM));
@@ -492,10 +493,10 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     CD* __restrict__ sbuf = static_cast<CD*>(a.s);
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = cconv<TF>(sbuf[base + t + q * Tl]);
-    line_dft<M, E, +1>(v, sm, si, t, tw);
     const TS alpha = TS(S.alpha);
     const TS eta = TS(a.eta);
     if (!a.solver) {
+      line_dft<M, E, +1>(v, sm, si, t, tw);
       CD* __restrict__ out = static_cast<CD*>(a.out);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
@@ -506,29 +507,41 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       }
       return;
     }
+    // every operand of the epilogue is loaded before the transform, so the
+    // loads overlap it instead of waiting behind its barriers
     const CS* __restrict__ Hphi = static_cast<const CS*>(a.t);
     CS* __restrict__ rprev = static_cast<CS*>(a.r_prev);
     const CD* __restrict__ pprev = static_cast<const CD*>(a.p);
+    CS ph[E], hq[E], ro[E];
+    CD pp[E];
+    TS vv[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const long long g = base + t + q * Tl;
+      ph[q] = phi[g];
+      hq[q] = Hphi[g];
+      ro[q] = rprev[g];
+      pp[q] = pprev[g];
+      vv[q] = V[g];
+    }
+    line_dft<M, E, +1>(v, sm, si, t, tw);
     const TS lam = TS(S.lam);
     TS a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
-      const CS ph = phi[g];
-      const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
+      const TS den = alpha + vv[q] + eta * (ph[q].x * ph[q].x + ph[q].y * ph[q].y);
       const CD Prd = cconv<TD>(cscale(cconv<TS>(v[q]), TS(1) / sqrt(den)));
       sbuf[g] = Prd;
       const CS Pr = cconv<TS>(Prd);  // the stored direction, as later passes see it
-      const CS h = Hphi[g];
-      const CS r = cmk<CS>(h.x - lam * ph.x, h.y - lam * ph.y);
-      const CS ro = rprev[g];
-      const CS pp = cconv<TS>(pprev[g]);
+      const CS r = cmk<CS>(hq[q].x - lam * ph[q].x, hq[q].y - lam * ph[q].y);
+      const CS pq = cconv<TS>(pp[q]);
       a0 += r.x * Pr.x + r.y * Pr.y;
-      a1 += (r.x - ro.x) * Pr.x + (r.y - ro.y) * Pr.y;
-      a2 += Pr.x * ph.x + Pr.y * ph.y;
-      a3 += pp.x * ph.x + pp.y * ph.y;
-      a4 += r.x * pp.x + r.y * pp.y;
-      a5 += r.x * ph.x + r.y * ph.y;
+      a1 += (r.x - ro[q].x) * Pr.x + (r.y - ro[q].y) * Pr.y;
+      a2 += Pr.x * ph[q].x + Pr.y * ph[q].y;
+      a3 += pq.x * ph[q].x + pq.y * ph[q].y;
+      a4 += r.x * pq.x + r.y * pq.y;
+      a5 += r.x * ph[q].x + r.y * ph[q].y;
       rprev[g] = r;
     }
     acc[0] = acc_add(acc[0], acc_from(a0)); acc[1] = acc_add(acc[1], acc_from(a1));
@@ -721,7 +734,7 @@ __device__ __forceinline__ void reduce_and_finish(const PassArgs& a, const Acc* 
 }
 
 template <typename TF, typename TS, typename TD, int M, int ROLE>
-__global__ void __launch_bounds__(MaxThreads<TF>::value) pass_x(PassArgs a) {
+__global__ void __launch_bounds__(MaxThreads<TF>::value < MaxThreads<TS>::value ? MaxThreads<TF>::value : MaxThreads<TS>::value) pass_x(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.solver && a.ctl->done) return;
   const Scal S = scal_of(a.ctl, a);
