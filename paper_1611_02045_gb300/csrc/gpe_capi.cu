@@ -519,10 +519,6 @@ static gpe_status run_persistent(gpe_ctx* c, int mode, bool* launched) {
   // SM (FP64 passes are bound by the per-SM FP64 rate), at most 256 threads
   int g = 1;
   while (2 * g * Tl <= 256 && nlines / (2 * g) >= c->nsm) g *= 2;
-  if (const char* ev = getenv("GPE_PERSIST_LINES")) {
-    const int v = atoi(ev);
-    if (v >= 1 && v * Tl <= 256 && (v & (v - 1)) == 0 && v <= nlines && v <= c->n[0]) g = v;
-  }
   if (g * Tl < 32 && 32 / Tl <= nlines && 32 / Tl <= c->n[0]) g = 32 / Tl;  // at least one warp
   const int block = g * Tl;
   IterArgs I = iter_args(c, mode, 0ull);
