@@ -346,3 +346,97 @@ def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterat
             break
     return phi, dict(status=status, iters=n, log=log, iterates=iterates,
                      E=log[-1]["E"], lam=log[-1]["lam"], res_inf=log[-1]["res_inf"])
+
+
+# --------------------------------------------------------------------------
+# Derivatives (Section 2: gradient, Hessian, tangent space of the sphere)
+# --------------------------------------------------------------------------
+
+
+def energy_gradient(prob, phi):
+    """Gradient of the discrete energy with respect to the real and imaginary
+    parts of the grid values, dE/dRe phi_k + i dE/dIm phi_k.
+
+    Section 2 gives nabla E(phi) = 2 H_phi phi for the weighted inner product
+    <f, g> = h^d sum conj(f) g; the coefficient-space gradient carries h^d."""
+    return 2.0 * prob.weight * apply_H(prob, phi, phi)
+
+
+def energy_parameter_derivatives(prob, phi):
+    """Partial derivatives of E(phi; V, eta, omega) at fixed phi:
+    dE/dV_k = h^d |phi_k|^2, dE/deta = 1/2 int |phi|^4, dE/domega = -<phi, L_z phi>.
+    At a normalised critical point the constraint contributes nothing, so these
+    are the derivatives of the ground-state energy (Hellmann-Feynman)."""
+    w = prob.weight
+    return dict(dV=w * np.abs(phi) ** 2,
+                deta=0.5 * w * np.sum(np.abs(phi) ** 4),
+                domega=-inner(prob, phi, Lz(prob, phi)).real)
+
+
+def hessian_apply(prob, phi, lam, f):
+    """K f = H_phi f + eta |phi|^2 f + eta phi^2 conj(f) - lam f: the operator of
+    the form 1/2 grad^2 E(phi)[f, f] - lam ||f||^2 of Section 2 (with the term
+    of reading R3), so that Re<f, K f> equals that form.  Real-linear in f."""
+    return (apply_H(prob, phi, f) + prob.eta * np.abs(phi) ** 2 * f
+            + prob.eta * phi ** 2 * np.conj(f) - lam * f)
+
+
+def tangent_project(prob, phi, h):
+    """Projection onto {h : <phi, h> = 0} for ||phi|| = 1: the tangent space
+    Re<phi, h> = 0 of Section 2 (projector M_phi) with the phase direction
+    i phi removed as well, since E and every density functional are invariant
+    under phi -> e^{i a} phi, so K (i phi) = 0 at a critical point."""
+    return h - inner(prob, phi, h) * phi
+
+
+def tangent_solve(prob, phi, lam, rhs, tol=1e-12, max_iter=5000, alpha=None):
+    """Solve K z = rhs for z with <phi, z> = 0 (rhs projected first), by the
+    conjugate gradient method in the real inner product Re<.,.>, preconditioned
+    by the projected P_C of eq. combinedP_12 (shift alpha, default lambda~ of
+    eq. Opt_Alpha).  Returns (z, iterations, relative residual)."""
+    if alpha is None:
+        alpha = lambda_tilde(prob, phi)
+    b = tangent_project(prob, phi, rhs)
+    bnorm = norm(prob, b)
+    z = np.zeros_like(b)
+    if bnorm == 0.0:
+        return z, 0, 0.0
+    r = b.copy()
+    y = tangent_project(prob, phi, precond_C(prob, phi, r, alpha))
+    p = y.copy()
+    ry = inner(prob, r, y).real
+    it, rel_res = 0, 1.0
+    while it < max_iter:
+        q = tangent_project(prob, phi, hessian_apply(prob, phi, lam, p))
+        a = ry / inner(prob, p, q).real
+        z = z + a * p
+        r = r - a * q
+        it += 1
+        rel_res = norm(prob, r) / bnorm
+        if rel_res < tol:
+            break
+        y = tangent_project(prob, phi, precond_C(prob, phi, r, alpha))
+        ry_new = inner(prob, r, y).real
+        p = y + (ry_new / ry) * p
+        ry = ry_new
+    return z, it, rel_res
+
+
+def density_loss(prob, phi, rho):
+    """L = int (|phi|^2 - rho)^2 (discrete: h^d sum)."""
+    return prob.weight * np.sum((np.abs(phi) ** 2 - rho) ** 2)
+
+
+def density_loss_gradient_V(prob, phi, rho, tol=1e-12, max_iter=5000):
+    """dL/dV_k for L(phi*(V)) with phi* a normalised ground state of V.
+
+    Differentiating H_phi phi = lambda phi with ||phi|| = 1 gives
+    K dphi = -(dV phi) on the tangent space, K as in hessian_apply.  With
+    g = 4 (|phi|^2 - rho) phi, the gradient of L for the weighted inner
+    product, the adjoint z = K^{-1} P g (P the projection of tangent_project)
+    yields dL = -Re<z, dV phi>, i.e. dL/dV_k = -h^d Re(conj(z_k) phi_k).
+    Returns (dL/dV, tangent_solve iterations, relative residual)."""
+    lam = inner(prob, phi, apply_H(prob, phi, phi)).real
+    g = 4.0 * (np.abs(phi) ** 2 - rho) * phi
+    z, it, res = tangent_solve(prob, phi, lam, g, tol=tol, max_iter=max_iter)
+    return -prob.weight * (np.conj(z) * phi).real, it, res

@@ -143,7 +143,7 @@ def random_field(seed, n, L):
 
 # --- the named workloads -----------------------------------------------------
 
-def workload(name: str):
+def workload(name: str, index: int = 0):
     """Return dict(n, L, eta, omega, V, phi0) for a named synthetic workload.
 
     c64_2d     : 64x64 on [-8,8]^2, V = r^2/2, eta = 100, omega = 0.5,
@@ -153,6 +153,10 @@ def workload(name: str):
     rot128_3d  : 128^3 on [-8,8]^3, V = (x^2+y^2+4z^2)/2, eta = 5000,
                  omega = 0.8, anisotropic Gaussian (1,1,2) times the vortex
                  factor mix (1-omega) + omega (x+iy), perturbed (seed 4).
+    grad256_2d : instance `index` (0..15) of the differentiation batch:
+                 256x256 on [-16,16]^2, eta = 500, omega = 0.7,
+                 V = r^2/2 + 0.1 S with S = smooth_bumps(seed 50 + index),
+                 phi_d + 1e-3 perturbation (seed 70 + index).
     """
     if name == "c64_2d":
         n, L = (64, 64), (8.0, 8.0)
@@ -172,4 +176,9 @@ def workload(name: str):
         G = ((1.0 - 0.8) + 0.8 * (m[0] + 1j * m[1])) * G
         phi0 = perturbed(normalise(G, n, L), 4, n, L)
         return dict(n=n, L=L, eta=5000.0, omega=0.8, V=V, phi0=phi0)
+    if name == "grad256_2d":
+        n, L = (256, 256), (16.0, 16.0)
+        V = harmonic(n, L) + 0.1 * smooth_bumps(n, L, 50 + index)
+        phi0 = perturbed(phi_d(n, L, 0.7), 70 + index, n, L)
+        return dict(n=n, L=L, eta=500.0, omega=0.7, V=V, phi0=phi0)
     raise KeyError(name)

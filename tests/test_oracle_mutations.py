@@ -23,6 +23,11 @@ QUICK_PINS = [
     P.test_P5_curvature_matches_second_difference,
     lambda: P.test_P6_preconditioner_hermitian_positive((16, 16)),
     P.test_P6_kinetic_preconditioner_inverts_shifted_laplacian,
+    P.test_P10_energy_gradient_matches_central_differences,
+    lambda: P.test_P10_parameter_derivatives_match_central_differences(0.0),
+    lambda: P.test_P11_hellmann_feynman_matches_differences_of_solves(P.solve_ground_state_16()),
+    lambda: P.test_P12_hessian_operator_is_the_second_order_form(P.solve_ground_state_16()),
+    lambda: P.test_P12_density_loss_gradient_matches_differences_of_solves(P.solve_ground_state_16()),
 ]
 
 
@@ -98,6 +103,37 @@ def _freq_twice(self, i):
     return 2.0 * _orig_freq(self, i)
 
 
+_orig_grad = O.energy_gradient
+_orig_pderiv = O.energy_parameter_derivatives
+_orig_hess = O.hessian_apply
+_orig_dloss = O.density_loss_gradient_V
+
+
+def _grad_unweighted(prob, phi):
+    return _orig_grad(prob, phi) / prob.weight
+
+
+def _domega_wrong_sign(prob, phi):
+    d = _orig_pderiv(prob, phi)
+    d["domega"] = -d["domega"]
+    return d
+
+
+def _deta_without_half(prob, phi):
+    d = _orig_pderiv(prob, phi)
+    d["deta"] = 2.0 * d["deta"]
+    return d
+
+
+def _hessian_without_conjugate_term(prob, phi, lam, f):
+    return _orig_hess(prob, phi, lam, f) - prob.eta * phi ** 2 * np.conj(f)
+
+
+def _dloss_wrong_sign(prob, phi, rho, tol=1e-12, max_iter=5000):
+    g, it, res = _orig_dloss(prob, phi, rho, tol, max_iter)
+    return -g, it, res
+
+
 MUTATIONS = {
     "Lz_sign": ("Lz", _lz_wrong_sign),
     "Lz_axes": ("Lz", _lz_swapped_axes),
@@ -108,6 +144,11 @@ MUTATIONS = {
     "deltaE_coeff": ("delta_energy", _delta_wrong_coefficient),
     "P_nonsymmetric": ("precond_C", _precond_nonsymmetric),
     "P_delta_shift": ("precond_delta", _delta_shift_wrong),
+    "grad_unweighted": ("energy_gradient", _grad_unweighted),
+    "domega_sign": ("energy_parameter_derivatives", _domega_wrong_sign),
+    "deta_no_half": ("energy_parameter_derivatives", _deta_without_half),
+    "hessian_no_conj": ("hessian_apply", _hessian_without_conjugate_term),
+    "dloss_sign": ("density_loss_gradient_V", _dloss_wrong_sign),
 }
 
 

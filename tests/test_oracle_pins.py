@@ -256,3 +256,111 @@ def test_P8_P9_invariants_and_stationarity():
     assert np.max(np.abs(Hphi - lam * phi)) < 1e-8
     # energy error is quadratic in the residual near the minimum
     assert abs(E[-1] - rep["E"]) == 0.0
+
+
+# ---------------------------------------------------------------- P10-P12: derivatives
+def _grad_problem(omega=0.3):
+    n, L = (16, 16), (4.0, 4.0)
+    V = I.harmonic(n, L) + 0.3 * I.smooth_bumps(n, L, 11)
+    return O.Problem(n, L, 10.0, omega, V)
+
+
+def test_P10_energy_gradient_matches_central_differences():
+    """energy_gradient is dE/dRe phi + i dE/dIm phi: central differences of the
+    energy along a real and an imaginary direction reproduce Re<g, d> (unweighted)."""
+    p = _grad_problem()
+    n, L = p.n, p.L
+    phi = I.normalise(I.phi_d(n, L, 0.5) * (1 + 0.2 * I.random_field(21, n, L)), n, L)
+    g = O.energy_gradient(p, phi)
+    eps = 1e-6
+    for d in (I.random_field(22, n, L).real + 0j, 1j * I.random_field(23, n, L).real):
+        fd = (O.energy(p, phi + eps * d) - O.energy(p, phi - eps * d)) / (2 * eps)
+        an = np.sum((np.conj(g) * d).real)
+        assert abs(fd - an) < 1e-7 * abs(an)
+
+
+@pytest.mark.parametrize("omega", [0.3, 0.0])
+def test_P10_parameter_derivatives_match_central_differences(omega):
+    """dE/dV, dE/deta, dE/domega at fixed phi against differences of the energy
+    in each parameter (omega = 0 included: the derivative is -<phi, L_z phi>)."""
+    p = _grad_problem(omega)
+    n, L = p.n, p.L
+    phi = I.normalise(I.phi_d(n, L, 0.5) * (1 + 0.2 * I.random_field(24, n, L)), n, L)
+    d = O.energy_parameter_derivatives(p, phi)
+    h = 1e-6
+
+    def E(eta=p.eta, om=p.omega, V=p.V):
+        return O.energy(O.Problem(n, L, eta, om, V), phi)
+
+    assert abs((E(eta=p.eta + h) - E(eta=p.eta - h)) / (2 * h) - d["deta"]) < 1e-7 * abs(d["deta"])
+    fd_om = (E(om=omega + h) - E(om=omega - h)) / (2 * h)
+    assert abs(d["domega"]) > 1e-3 and abs(fd_om - d["domega"]) < 1e-7 * abs(d["domega"])
+    S = I.smooth_bumps(n, L, 13)
+    fd_V = (E(V=p.V + h * S) - E(V=p.V - h * S)) / (2 * h)
+    assert abs(fd_V - np.sum(d["dV"] * S)) < 1e-7 * abs(fd_V)
+
+
+def solve_ground_state_16():
+    p = _grad_problem()
+    phi0 = I.perturbed(I.phi_a(p.n, p.L), 12, p.n, p.L, amp=1e-2)
+    phi, rep = O.pcg_solve(p, phi0, O.SolveOptions(tol_res_inf=1e-12))
+    assert rep["status"] == "converged"
+    return p, phi
+
+
+@pytest.fixture(scope="module")
+def ground_state_16():
+    return solve_ground_state_16()
+
+
+def _resolve(p, phi_start, eta=None, omega=None, dV=0.0):
+    q = O.Problem(p.n, p.L, p.eta if eta is None else eta, p.omega if omega is None else omega, p.V + dV)
+    f, rep = O.pcg_solve(q, phi_start, O.SolveOptions(tol_res_inf=1e-12))
+    assert rep["status"] == "converged"
+    return f, rep["E"]
+
+
+def test_P11_hellmann_feynman_matches_differences_of_solves(ground_state_16):
+    """At a ground state, the fixed-phi derivatives equal the derivatives of the
+    ground-state energy E*(eta, omega, V), obtained here by re-solving the
+    perturbed problems (warm start at phi*) and central differences."""
+    p, phi = ground_state_16
+    d = O.energy_parameter_derivatives(p, phi)
+    h = 1e-5
+    fd = (_resolve(p, phi, eta=p.eta + h)[1] - _resolve(p, phi, eta=p.eta - h)[1]) / (2 * h)
+    assert abs(fd - d["deta"]) < 1e-7 * abs(d["deta"])
+    fd = (_resolve(p, phi, omega=p.omega + h)[1] - _resolve(p, phi, omega=p.omega - h)[1]) / (2 * h)
+    assert abs(fd - d["domega"]) < 1e-5 * abs(d["domega"])
+    S = I.smooth_bumps(p.n, p.L, 13)
+    fd = (_resolve(p, phi, dV=h * S)[1] - _resolve(p, phi, dV=-h * S)[1]) / (2 * h)
+    assert abs(fd - np.sum(d["dV"] * S)) < 1e-7 * abs(fd)
+
+
+def test_P12_hessian_operator_is_the_second_order_form(ground_state_16):
+    """Re<f, K f> = 1/2 grad^2 E[f, f] - lam ||f||^2 (Section 2), and the phase
+    direction i phi is in the kernel of K at a critical point."""
+    p, phi = ground_state_16
+    lam = O.chemical_potential(p, phi)
+    f = I.random_field(31, p.n, p.L)
+    lhs = O.inner(p, f, O.hessian_apply(p, phi, lam, f)).real
+    rhs = O.hessian_form(p, phi, f) - lam * O.inner(p, f, f).real
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+    k = O.hessian_apply(p, phi, lam, 1j * phi)
+    assert O.norm(p, k) < 1e-10
+
+
+def test_P12_density_loss_gradient_matches_differences_of_solves(ground_state_16):
+    """The tangent-space adjoint gradient of L = int (|phi*|^2 - rho)^2 with
+    respect to V against central differences of L over re-solved ground states."""
+    p, phi = ground_state_16
+    rho = np.abs(I.normalise(I.anisotropic_gaussian(p.n, p.L, [1.3, 0.8]), p.n, p.L)) ** 2
+    gV, it, res = O.density_loss_gradient_V(p, phi, rho)
+    assert res < 1e-12 and it < 200
+    h = 1e-5
+    for seed in (13, 14):
+        S = I.smooth_bumps(p.n, p.L, seed)
+        fp, _ = _resolve(p, phi, dV=h * S)
+        fm, _ = _resolve(p, phi, dV=-h * S)
+        fd = (O.density_loss(p, fp, rho) - O.density_loss(p, fm, rho)) / (2 * h)
+        an = np.sum(gV * S)
+        assert abs(fd - an) < 1e-5 * abs(an)
