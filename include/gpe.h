@@ -172,6 +172,74 @@ gpe_status gpe_precond(gpe_ctx* ctx, const void* phi_dev, const void* r_dev, dou
  * Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
 gpe_status gpe_energy(gpe_ctx* ctx, const void* phi_dev, double out[8]);
 
+/* Replace the context's potential and coupling constants without
+ * re-creating it (parameter sweeps, finite differences, fitting V).
+ *  V     : new real potential, float64 [z][y][x], host or device; NULL keeps
+ *          the current one.  Must be finite.
+ *  eta, omega : new nonlinearity and rotation speed (Section 2), finite.
+ * Every later call uses the new problem; CUDA graphs captured for the old one
+ * are discarded.  Synchronises the stream.  Errors: GPE_ERR_ARG,
+ * GPE_ERR_CUDA. */
+gpe_status gpe_set_problem(gpe_ctx* ctx, const double* V, double eta, double omega);
+
+/* Derivatives of the discrete energy (Section 2, with the discretisation of
+ * Section 3) at phi, for phi held fixed:
+ *  grad_phi_dev : if not NULL, receives nabla E(phi) = 2 h^d H_phi phi, the
+ *                 gradient of E with respect to the real and imaginary parts
+ *                 of the grid values (d E / d Re phi_k + i d E / d Im phi_k);
+ *                 Section 2 gives nabla E = 2 H_phi phi for the weighted inner
+ *                 product, h^d converts it to the coefficient vector.  Field
+ *                 in working precision; must not overlap phi.
+ *  grad_V_dev   : if not NULL, float64 [z][y][x]: d E / d V_k = h^d |phi_k|^2.
+ *  out          : out[0] E, out[1] d E / d eta = 1/2 int |phi|^4,
+ *                 out[2] d E / d omega = -<phi, L_z phi>, out[3] lambda =
+ *                 <phi, H_phi phi>, out[4] ||phi||^2.
+ * At a normalised critical point phi* (a ground state from gpe_pcg_solve) the
+ * constraint terms vanish, so out[1], out[2] and grad_V are the derivatives
+ * of the ground-state energy E*(V, eta, omega) itself (Hellmann-Feynman).
+ * Synchronises the stream.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
+gpe_status gpe_energy_grad(gpe_ctx* ctx, const void* phi_dev, void* grad_phi_dev, double* grad_V_dev, double out[5]);
+
+/* Tangent-space adjoint solve at a ground state: find z with <phi, z> = 0 and
+ *   P K z = P rhs,   K f = H_phi f + eta |phi|^2 f + eta phi^2 conj(f) - lambda f,
+ * P h = h - <phi, h> phi.  K is the operator of the second-order form
+ * 1/2 grad^2 E(phi)[f, f] - lambda ||f||^2 of Section 2 (with the term
+ * eta int |phi|^2 |f|^2 the printed formula omits), lambda = <phi, H_phi phi>;
+ * P is the tangent projector M_phi of Section 2 with the phase direction
+ * i phi also removed (K (i phi) = 0 at a critical point).  Section 2's
+ * second-order condition makes K positive on that space at a local minimum.
+ * Differentiating H_phi phi = lambda phi, ||phi|| = 1 gives K dphi = -P(dV phi),
+ * so with rhs = the weighted gradient of a loss L(phi) (dL = Re<rhs, dphi>),
+ * dL/dV_k = -h^d Re(conj(z_k) phi_k).
+ * Method: conjugate gradients in the real inner product Re<.,.>, the
+ * preconditioner P P_C P (eq. combinedP_12 with the shift lambda~ of eq.
+ * Opt_Alpha at phi), stopped when ||r|| <= tol ||P rhs||.
+ *  phi_dev : normalised ground state (working precision);
+ *  rhs_dev : right-hand side (working precision);
+ *  z_dev   : solution (working precision), must not overlap phi or rhs;
+ *  iters, rel_res : may be NULL; iterations and ||r|| / ||P rhs||.
+ * Synchronises the stream.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA,
+ * GPE_ERR_NOT_CONVERGED (max_iter reached; z holds the last iterate),
+ * GPE_ERR_NONFINITE (K or P_C not positive -- phi is not a local minimum --
+ * or a non-finite residual). */
+gpe_status gpe_tangent_solve(gpe_ctx* ctx, const void* phi_dev, const void* rhs_dev, void* z_dev, double tol,
+                             int max_iter, int* iters, double* rel_res);
+
+/* Gradient with respect to V of a loss L(rho) of the ground-state density
+ * rho = |phi*|^2, through the tangent-space adjoint solve above:
+ *   rhs = (2 / h^d) g_rho phi  (so that dL = Re<rhs, dphi>),
+ *   z   = gpe_tangent_solve(phi, rhs),
+ *   grad_V[k] = dL/dV_k = -h^d Re(conj(z_k) phi_k).
+ *  phi_dev    : normalised ground state for the context's V, eta, omega
+ *               (working precision);
+ *  g_rho_dev  : float64 dL/drho_k per grid point (device);
+ *  grad_V_dev : float64 output (device).
+ * tol, max_iter, iters, rel_res as for gpe_tangent_solve.  Synchronises the
+ * stream.  Errors as gpe_tangent_solve; on GPE_ERR_NOT_CONVERGED grad_V is
+ * computed from the last iterate. */
+gpe_status gpe_density_adjoint(gpe_ctx* ctx, const void* phi_dev, const double* g_rho_dev, double* grad_V_dev,
+                               double tol, int max_iter, int* iters, double* rel_res);
+
 /* Ground state by Algorithm 2 (PCG) with the symmetric combined
  * preconditioner P_C, the Polak-Ribiere coefficient beta = max(beta_PR, 0)
  * (eq. CG:PR), the descent check of Section 5.2, the step-size heuristic and

@@ -72,6 +72,10 @@ struct gpe_ctx {
   int pers_max_grid = 0;
   int last_loop = -1;  // loop style the last solve phase ran (gpe_report.loop_kind)
   cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // per launch mode
+  // tangent-space adjoint workspace (allocated by the first gpe_tangent_solve)
+  void* adj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // r, y, p, q, rhs, z
+  AdjScalars* adj_s = nullptr;
+  double* adj_partials = nullptr;
 };
 
 #define GPE_CU(ctx, call)                                                                  \
@@ -192,6 +196,38 @@ static cudaError_t upload_tables(gpe_ctx* c, PrecBufs& b) {
   return cudaSuccess;
 }
 
+// V of one precision (float32, float64 or double-single) from a device float64
+// copy; the buffer is already allocated.
+static gpe_status upload_V(gpe_ctx* c, int prec, const double* Vdev64) {
+  PrecBufs& b = c->pb[prec];
+  if (prec == 2) GPE_CU(c, launch_d2ds(Vdev64, b.V, c->N, 0));
+  else if (prec == 1) GPE_CU(c, cudaMemcpy(b.V, Vdev64, 8 * (size_t)c->N, cudaMemcpyDeviceToDevice));
+  else GPE_CU(c, launch_d2f(Vdev64, (float*)b.V, c->N, 0));
+  GPE_CU(c, cudaDeviceSynchronize());
+  return GPE_OK;
+}
+
+// Copy V (float64, host or device) to a new device buffer, check that it is
+// finite and record its maximum (used by the single-precision floor estimate).
+static gpe_status load_V(gpe_ctx* c, const double* V, double** V64_out) {
+  *V64_out = nullptr;
+  double* V64 = nullptr;
+  if (cudaMalloc(&V64, 8 * (size_t)c->N) != cudaSuccess) { c->err = "cudaMalloc V"; return GPE_ERR_CUDA; }
+  std::vector<double> Vh((size_t)c->N);
+  if (cudaMemcpy(V64, V, 8 * (size_t)c->N, cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(Vh.data(), V64, 8 * (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaFree(V64); c->err = "copy of V failed"; return GPE_ERR_CUDA;
+  }
+  double vm = -1e300;
+  for (double v : Vh) {
+    if (!std::isfinite(v)) { cudaFree(V64); c->err = "V must be finite"; return GPE_ERR_ARG; }
+    vm = v > vm ? v : vm;
+  }
+  c->vmax = vm;
+  *V64_out = V64;
+  return GPE_OK;
+}
+
 static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
   PrecBufs& b = c->pb[prec];
   b.on = true;
@@ -206,19 +242,8 @@ static gpe_status alloc_prec(gpe_ctx* c, int prec, const double* Vdev64) {
   GPE_CU(c, cudaMalloc(&b.r_prev, bytes));
   GPE_CU(c, cudaMemset(b.p, 0, bytes));
   GPE_CU(c, cudaMemset(b.r_prev, 0, bytes));
-  if (prec == 2) {
-    GPE_CU(c, cudaMalloc(&b.V, 8 * (size_t)c->N));
-    GPE_CU(c, launch_d2ds(Vdev64, b.V, c->N, 0));
-    GPE_CU(c, cudaDeviceSynchronize());
-  } else if (prec == 1) {
-    GPE_CU(c, cudaMalloc(&b.V, 8 * (size_t)c->N));
-    GPE_CU(c, cudaMemcpy(b.V, Vdev64, 8 * (size_t)c->N, cudaMemcpyDeviceToDevice));
-  } else {
-    GPE_CU(c, cudaMalloc(&b.V, 4 * (size_t)c->N));
-    GPE_CU(c, launch_d2f(Vdev64, (float*)b.V, c->N, 0));
-    GPE_CU(c, cudaDeviceSynchronize());
-  }
-  return GPE_OK;
+  GPE_CU(c, cudaMalloc(&b.V, (prec == 0 ? 4 : 8) * (size_t)c->N));
+  return upload_V(c, prec, Vdev64);
 }
 
 static void free_ctx(gpe_ctx* c) {
@@ -229,6 +254,8 @@ static void free_ctx(gpe_ctx* c) {
     cudaFree(b.V); cudaFree(b.phi); cudaFree(b.p); cudaFree(b.t); cudaFree(b.s); cudaFree(b.r_prev);
   }
   cudaFree(c->pers_partials); cudaFree(c->pers_bar);
+  for (auto& a : c->adj) cudaFree(a);
+  cudaFree(c->adj_s); cudaFree(c->adj_partials);
   cudaFree(c->ctl_solve); cudaFree(c->ctl_api); cudaFree(c->partials); cudaFree(c->ticket); cudaFree(c->log_dev);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
@@ -277,23 +304,11 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
   auto fail = [&](gpe_status s) { g_create_error = c->err; free_ctx(c); return s; };
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) { c->err = "stream create failed"; return fail(GPE_ERR_CUDA); }
 
-  // potential: keep a device float64 copy as the source of both precisions
+  // potential: a device float64 copy is the source of every precision
   double* V64 = nullptr;
-  if (cudaMalloc(&V64, 8 * (size_t)c->N) != cudaSuccess) { c->err = "cudaMalloc V"; return fail(GPE_ERR_CUDA); }
-  if (cudaMemcpy(V64, V, 8 * (size_t)c->N, cudaMemcpyDefault) != cudaSuccess) {
-    cudaFree(V64); c->err = "copy of V failed"; return fail(GPE_ERR_CUDA);
-  }
   {
-    std::vector<double> Vh((size_t)c->N);
-    if (cudaMemcpy(Vh.data(), V64, 8 * (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess) {
-      cudaFree(V64); c->err = "copy of V failed"; return fail(GPE_ERR_CUDA);
-    }
-    double vm = -1e300;
-    for (double v : Vh) {
-      if (!std::isfinite(v)) { cudaFree(V64); c->err = "V must be finite"; return fail(GPE_ERR_ARG); }
-      vm = v > vm ? v : vm;
-    }
-    c->vmax = vm;
+    const gpe_status sv = load_V(c, V, &V64);
+    if (sv != GPE_OK) return fail(sv);
   }
   gpe_status s = alloc_prec(c, 1, V64);
   if (s == GPE_OK && prob->prec == GPE_MIXED) s = alloc_prec(c, 0, V64);
@@ -395,6 +410,55 @@ extern "C" gpe_status gpe_energy(gpe_ctx* c, const void* phi, double out[8]) {
   return GPE_OK;
 }
 
+extern "C" gpe_status gpe_set_problem(gpe_ctx* c, const double* V, double eta, double omega) {
+  if (!c) return GPE_ERR_ARG;
+  if (!std::isfinite(eta) || !std::isfinite(omega)) { c->err = "eta/omega must be finite"; return GPE_ERR_ARG; }
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  if (V) {
+    double* V64 = nullptr;
+    gpe_status s = load_V(c, V, &V64);
+    if (s != GPE_OK) return s;
+    for (int prec = 0; prec < 3 && s == GPE_OK; ++prec)
+      if (c->pb[prec].on) s = upload_V(c, prec, V64);
+    cudaFree(V64);
+    if (s != GPE_OK) return s;
+  }
+  c->prob.eta = eta;
+  c->prob.omega = omega;
+  // captured graphs hold the old eta and omega in their kernel arguments
+  for (auto& e : c->exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_energy_grad(gpe_ctx* c, const void* phi, void* grad_phi, double* grad_V, double out[5]) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !out) { c->err = "null pointer"; return GPE_ERR_ARG; }
+  if (grad_phi == phi) { c->err = "grad_phi must not overlap phi"; return GPE_ERR_ARG; }
+  const int prec = c->work;
+  void* hphi = grad_phi ? grad_phi : c->pb[prec].t;
+  gpe_status s = run_H(c, prec, phi, phi, hphi, c->ctl_api);
+  if (s != GPE_OK) return s;
+  if (grad_phi || grad_V) GPE_CU(c, launch_grad_epilogue(prec, phi, grad_phi, grad_V, c->N, c->weight, c->st));
+  Ctl h;
+  GPE_CU(c, cudaMemcpyAsync(&h, c->ctl_api, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  out[0] = h.E;
+  out[1] = 0.5 * h.U0;  // d/d eta of eta/2 int |phi|^4
+  out[2] = -h.Lz;       // d/d omega of -omega <phi, L_z phi>
+  out[3] = h.lam;
+  out[4] = h.norm2;
+  return GPE_OK;
+}
+
+// Tangent-space adjoint solve: K z = P rhs, <phi, z> = 0, by the projected
+// conjugate gradient method with the projected P_C as preconditioner (kernels
+// in gpe_adjoint.cu).  Declared below run_PC.
+static gpe_status tangent_solve(gpe_ctx* c, const void* phi, const void* rhs, void* z, double tol, int max_iter,
+                                int* iters, double* rel_res);
+
 // P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
 static gpe_status run_PC(gpe_ctx* c, const IterBufs& b, const void* r, double alpha, void* out, Ctl* ctl,
                          bool solver, cudaStream_t st) {
@@ -432,6 +496,113 @@ extern "C" gpe_status gpe_precond(gpe_ctx* c, const void* phi, const void* r, do
   IterBufs b = iter_bufs(c, prec);
   b.phi = const_cast<void*>(phi);
   return run_PC(c, b, r, alpha, out, c->ctl_api, false, c->st);
+}
+
+constexpr int kAdjMaxBlocks = 1024;
+constexpr int kAdjCheckEvery = 4;  // iterations between host reads of the scalars
+
+static gpe_status tangent_solve(gpe_ctx* c, const void* phi, const void* rhs, void* z, double tol, int max_iter,
+                                int* iters, double* rel_res) {
+  const int prec = c->work;
+  const size_t bytes = (prec ? 16 : 8) * (size_t)c->N;
+  if (!c->adj_s) {
+    for (auto& a : c->adj) GPE_CU(c, cudaMalloc(&a, bytes));
+    GPE_CU(c, cudaMalloc(&c->adj_s, sizeof(AdjScalars)));
+    GPE_CU(c, cudaMalloc(&c->adj_partials, sizeof(double) * 6 * kAdjMaxBlocks));
+  }
+  void *r = c->adj[0], *y = c->adj[1], *p = c->adj[2], *q = c->adj[3];
+  AdjScalars* S = c->adj_s;
+  const long long N = c->N;
+  const double w = c->weight;
+  cudaStream_t st = c->st;
+  // lambda = <phi, H phi> and the shift lambda~ of eq. Opt_Alpha at phi
+  gpe_status s = run_H(c, prec, phi, phi, q, c->ctl_api);
+  if (s != GPE_OK) return s;
+  Ctl h;
+  GPE_CU(c, cudaMemcpyAsync(&h, c->ctl_api, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  GPE_CU(c, cudaStreamSynchronize(st));
+  const double lam = h.lam, alpha = h.alpha;
+  if (!std::isfinite(lam) || !(alpha > 0.0)) { c->err = "phi gives a non-finite lambda or a shift <= 0"; return GPE_ERR_NONFINITE; }
+  AdjScalars s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.tol2 = tol * tol;
+  GPE_CU(c, cudaMemcpyAsync(S, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+  GPE_CU(c, cudaMemsetAsync(z, 0, bytes, st));
+  GPE_CU(c, cudaMemsetAsync(p, 0, bytes, st));
+  // r = P rhs, bb = ||r||^2
+  GPE_CU(c, adj_dots(prec, phi, rhs, nullptr, nullptr, nullptr, nullptr, N, w, ADJ_PROJ, S, c->adj_partials,
+                     kAdjMaxBlocks, st));
+  GPE_CU(c, adj_proj(prec, rhs, r, phi, N, S, st));
+  GPE_CU(c, adj_dots(prec, r, r, nullptr, nullptr, nullptr, nullptr, N, w, ADJ_BB, S, c->adj_partials, kAdjMaxBlocks, st));
+  IterBufs b = iter_bufs(c, prec);
+  b.phi = const_cast<void*>(phi);
+  // y = P_C r; p = P y
+  if ((s = run_PC(c, b, r, alpha, y, c->ctl_api, false, st)) != GPE_OK) return s;
+  GPE_CU(c, adj_dots(prec, phi, y, r, y, r, phi, N, w, ADJ_RY_FIRST, S, c->adj_partials, kAdjMaxBlocks, st));
+  GPE_CU(c, adj_dir(prec, p, y, phi, N, S, st));
+  AdjScalars hs = s0;
+  int it = 0;
+  for (;;) {
+    if (it % kAdjCheckEvery == 0 || it >= max_iter) {
+      GPE_CU(c, cudaMemcpyAsync(&hs, S, sizeof(hs), cudaMemcpyDeviceToHost, st));
+      GPE_CU(c, cudaStreamSynchronize(st));
+      if (hs.stop || it >= max_iter) break;
+    }
+    // q = P K p;  a = Re<r, y> / Re<p, q>;  z += a p;  r -= a q
+    if ((s = run_H(c, prec, phi, p, q, c->ctl_api)) != GPE_OK) return s;
+    GPE_CU(c, adj_hess_epi(prec, phi, p, q, N, c->prob.eta, lam, w, S, c->adj_partials, kAdjMaxBlocks, st));
+    GPE_CU(c, adj_step(prec, z, r, p, q, phi, N, w, S, c->adj_partials, kAdjMaxBlocks, st));
+    // y = P_C r;  beta = Re<r, P y> / previous;  p = P y + beta p
+    if ((s = run_PC(c, b, r, alpha, y, c->ctl_api, false, st)) != GPE_OK) return s;
+    GPE_CU(c, adj_dots(prec, phi, y, r, y, r, phi, N, w, ADJ_RY, S, c->adj_partials, kAdjMaxBlocks, st));
+    GPE_CU(c, adj_dir(prec, p, y, phi, N, S, st));
+    ++it;
+  }
+  if (iters) *iters = hs.iters;
+  const double rr = hs.bb > 0.0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+  if (rel_res) *rel_res = rr;
+  if (hs.bad) {
+    c->err = hs.bad == 1 ? "Re<p, K p> <= 0: phi is not a local minimum (K not positive on the tangent space)"
+           : hs.bad == 2 ? "Re<r, P_C r> <= 0: preconditioner not positive"
+                         : "non-finite residual";
+    return GPE_ERR_NONFINITE;
+  }
+  if (!(rr <= tol)) {
+    c->err = "tangent solve reached max_iter";
+    return GPE_ERR_NOT_CONVERGED;
+  }
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_tangent_solve(gpe_ctx* c, const void* phi, const void* rhs, void* z, double tol, int max_iter,
+                                        int* iters, double* rel_res) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !rhs || !z) { c->err = "null field pointer"; return GPE_ERR_ARG; }
+  if (z == phi || z == rhs) { c->err = "z must not overlap phi or rhs"; return GPE_ERR_ARG; }
+  if (!(tol > 0.0) || max_iter < 1) { c->err = "tol must be > 0 and max_iter >= 1"; return GPE_ERR_ARG; }
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  return tangent_solve(c, phi, rhs, z, tol, max_iter, iters, rel_res);
+}
+
+extern "C" gpe_status gpe_density_adjoint(gpe_ctx* c, const void* phi, const double* g_rho, double* grad_V, double tol,
+                                          int max_iter, int* iters, double* rel_res) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi || !g_rho || !grad_V) { c->err = "null pointer"; return GPE_ERR_ARG; }
+  if (!(tol > 0.0) || max_iter < 1) { c->err = "tol must be > 0 and max_iter >= 1"; return GPE_ERR_ARG; }
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  const int prec = c->work;
+  const size_t bytes = (prec ? 16 : 8) * (size_t)c->N;
+  for (int i = 4; i < 6; ++i)
+    if (!c->adj[i]) GPE_CU(c, cudaMalloc(&c->adj[i], bytes));
+  void *rhs = c->adj[4], *z = c->adj[5];
+  GPE_CU(c, adj_density_rhs(prec, phi, g_rho, rhs, c->N, 2.0 / c->weight, c->st));
+  gpe_status s = tangent_solve(c, phi, rhs, z, tol, max_iter, iters, rel_res);
+  if (s != GPE_OK && s != GPE_ERR_NOT_CONVERGED) return s;
+  GPE_CU(c, adj_dV_from_z(prec, phi, z, grad_V, c->N, c->weight, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  return s;
 }
 
 // The pass arguments of one PCG iteration in launch mode `mode`, on the solver

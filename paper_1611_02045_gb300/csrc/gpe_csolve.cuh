@@ -56,15 +56,15 @@ __device__ __forceinline__ void cs_yunit(const cgc::cluster_group& cl, int rank,
   line_dft<M, E, -1>(w, xs, si, t, tw);
   if constexpr (ROLE == P_HMID || ROLE == P_AMID) {
     const float om = float(a.omega);
-    const float rs = -om * static_cast<const float*>(a.xc[0])[x];
-    float akin = 0.f, arot = 0.f;
+    const float rx = -static_cast<const float*>(a.xc[0])[x];
+    float akin = 0.f, arot = 0.f;  // arot: rotation symbol with omega (A p) or without it (H phi, finalize_H applies it)
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const float k = xiy[t + q * Tl];
-      const float mk = 0.5f * k * k, mr = rs * k;
+      const float mk = 0.5f * k * k, kr = rx * k, mr = om * kr;
       const float a2 = w[q].x * w[q].x + w[q].y * w[q].y;
       akin += mk * a2;
-      arot += mr * a2;
+      arot += (ROLE == P_AMID ? mr : kr) * a2;
       w[q] = cscale(w[q], (mk + mr) * invM);
     }
     if constexpr (ROLE == P_AMID) {

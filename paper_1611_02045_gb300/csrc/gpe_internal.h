@@ -32,6 +32,7 @@ struct Ctl {
   int stop_dE;     // energy criterion met at the last step
   // ---- per-iterate scalars ----
   double kin, rot, pot, U0, norm2;      // <phi,-Lap/2 phi>, <phi,-omega Lz phi>, <phi,V phi>, int|phi|^4, ||phi||^2
+  double Lz;                            // <phi, L_z phi> (real: L_z is Hermitian)
   double lam, alpha, E;                 // lambda_n, lambda~_n, E_n
   double res_inf, res_l2;
   double rPr, rPr_prev;                 // <r_n, P r_n>, previous
@@ -139,5 +140,40 @@ cudaError_t launch_convert_ds_to_c128(const void* src, void* dst, long long n, c
 // that the next H pass normalises phi in place.
 // prec: 0 complex64, 1 complex128, 2 double-single.
 cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st);
+// Tangent-space adjoint solve (gpe_adjoint.cu): device scalars of the
+// projected conjugate gradient iteration, and its kernels.  Each reduction
+// launcher sums weighted inner products into S and runs the scalar step
+// `stage`; update kernels read their coefficients from S and do nothing once
+// S->stop is set (converged: ||r||^2 <= tol2 ||r_0||^2, or broken down: bad).
+struct AdjScalars {
+  double c_re, c_im;  // projection coefficient <phi, h> of the last projected field
+  double a, beta;     // step length and conjugation coefficient
+  double ry, rr, bb, pq, tol2;
+  int bad;    // 1: Re<p, K p> <= 0; 2: Re<r, P_C r> <= 0; 3: non-finite residual
+  int stop;
+  int iters;
+};
+enum AdjStage { ADJ_PROJ = 0, ADJ_BB = 1, ADJ_PQ = 2, ADJ_RR = 3, ADJ_RY = 4, ADJ_RY_FIRST = 5 };
+cudaError_t adj_dots(int prec, const void* x0, const void* y0, const void* x1, const void* y1, const void* x2,
+                     const void* y2, long long n, double weight, int stage, AdjScalars* S, double* partials,
+                     int max_blocks, cudaStream_t st);
+cudaError_t adj_hess_epi(int prec, const void* phi, const void* p, void* q, long long n, double eta, double lam,
+                         double weight, AdjScalars* S, double* partials, int max_blocks, cudaStream_t st);
+cudaError_t adj_step(int prec, void* z, void* r, const void* p, const void* q, const void* phi, long long n,
+                     double weight, AdjScalars* S, double* partials, int max_blocks, cudaStream_t st);
+cudaError_t adj_proj(int prec, const void* h_in, void* h_out, const void* phi, long long n, const AdjScalars* S,
+                     cudaStream_t st);
+cudaError_t adj_dir(int prec, void* p, const void* y, const void* phi, long long n, const AdjScalars* S,
+                    cudaStream_t st);
+// rhs = s g_rho phi; grad_V = -weight Re(conj(z) phi)
+cudaError_t adj_density_rhs(int prec, const void* phi, const double* g_rho, void* rhs, long long n, double s,
+                            cudaStream_t st);
+cudaError_t adj_dV_from_z(int prec, const void* phi, const void* z, double* gV, long long n, double weight,
+                          cudaStream_t st);
+
+// grad_phi <- 2 weight grad_phi (in place), grad_V = weight |phi|^2 (float64);
+// prec 0 complex64, 1 complex128; null outputs are skipped.
+cudaError_t launch_grad_epilogue(int prec, const void* phi, void* gphi, double* gV, long long n, double weight,
+                                 cudaStream_t st);
 
 }  // namespace gpe

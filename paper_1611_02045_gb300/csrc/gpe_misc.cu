@@ -100,6 +100,38 @@ cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t 
   return cudaGetLastError();
 }
 
+// Epilogue of gpe_energy_grad: grad_phi <- 2 h^d H_phi phi in place (Section 2,
+// nabla E = 2 H_phi phi, h^d converting to the coefficient vector) and
+// grad_V = h^d |phi|^2.  Either output may be null.
+template <typename C>
+__global__ void k_grad_epilogue(const C* __restrict__ phi, C* __restrict__ gphi, double* __restrict__ gV, long long n,
+                                double weight) {
+  using R = decltype(C::x);
+  const R two_w = R(2.0 * weight);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (gphi) {
+      const C h = gphi[i];
+      C g;
+      g.x = two_w * h.x;
+      g.y = two_w * h.y;
+      gphi[i] = g;
+    }
+    if (gV) {
+      const C v = phi[i];
+      const double re = (double)v.x, im = (double)v.y;
+      gV[i] = weight * (re * re + im * im);
+    }
+  }
+}
+cudaError_t launch_grad_epilogue(int prec, const void* phi, void* gphi, double* gV, long long n, double weight,
+                                 cudaStream_t st) {
+  if (prec == 1)
+    k_grad_epilogue<double2><<<grid_for(n), 256, 0, st>>>((const double2*)phi, (double2*)gphi, gV, n, weight);
+  else
+    k_grad_epilogue<float2><<<grid_for(n), 256, 0, st>>>((const float2*)phi, (float2*)gphi, gV, n, weight);
+  return cudaGetLastError();
+}
+
 // One block, fixed-order FP64 sum of |phi|^2 (runs once per solve phase).
 template <typename C>
 __global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, long long n, double weight, Ctl* ctl) {

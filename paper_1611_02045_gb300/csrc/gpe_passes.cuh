@@ -176,11 +176,11 @@ __device__ __forceinline__ bool grid_reduce(Acc (&v)[K], const PassArgs& a, doub
 // ---------------------------------------------------------------------------
 // Constants the scalar steps need (from the pass arguments).
 struct Fin {
-  double weight, eta;
+  double weight, eta, omega;
   int dim, solver;
 };
 
-__device__ __forceinline__ Fin fin_of(const PassArgs& a) { return Fin{a.weight, a.eta, a.dim, a.solver}; }
+__device__ __forceinline__ Fin fin_of(const PassArgs& a) { return Fin{a.weight, a.eta, a.omega, a.dim, a.solver}; }
 
 // Row n of the iteration log, or null (no log, full, or not the writing block).
 __device__ __forceinline__ double* log_row(Ctl* c, bool writer) {
@@ -190,10 +190,11 @@ __device__ __forceinline__ double* log_row(Ctl* c, bool writer) {
 // After the last H pass: energy terms, lambda_n, lambda~_n, E_n (Section 2, eq. Opt_Alpha).
 static __device__ void finalize_H(Ctl* c, const Fin& a, bool writer) {
   const double w = a.weight;
-  double kin = 0.0, rot = 0.0;
-  for (int ax = 0; ax < a.dim; ++ax) { kin += c->hsum[ax][0]; rot += c->hsum[ax][1]; }
+  double kin = 0.0, lz = 0.0;
+  for (int ax = 0; ax < a.dim; ++ax) { kin += c->hsum[ax][0]; lz += c->hsum[ax][1]; }
   c->kin = w * kin;
-  c->rot = w * rot;
+  c->Lz = -w * lz;          // <phi, L_z phi>: the passes sum the symbol without omega
+  c->rot = -a.omega * c->Lz;
   c->pot = w * c->hsum[0][2];
   c->U0 = w * c->hsum[0][3];
   c->norm2 = w * c->hsum[0][4];
@@ -432,14 +433,14 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     line_dft<M, E, -1>(v, sm, si, t, tw);
     const TF y = tab<TF>(a.xc[1])[iy];
     const TF om = TF(a.omega);
-    TF akin = 0, arot = 0;
+    TF akin = 0, arot = 0;  // arot: the rotation symbol without omega (omega is applied in finalize_H)
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const TF k = xi[t + q * Tl];
-      const TF mk = TF(0.5) * k * k, mr = om * y * k;
+      const TF mk = TF(0.5) * k * k, kr = y * k;
       const TF a2 = v[q].x * v[q].x + v[q].y * v[q].y;
-      akin += mk * a2; arot += mr * a2;
-      v[q] = cscale(v[q], (mk + mr) * invM);
+      akin += mk * a2; arot += kr * a2;
+      v[q] = cscale(v[q], (mk + om * kr) * invM);
     }
     line_dft<M, E, +1>(v, sm, si, t, tw);
     CS* __restrict__ tout = static_cast<CS*>(a.t);
@@ -621,15 +622,15 @@ __device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long lon
     line_dft<M, E, -1>(v, sm, si, t, tw);
     const T om = T(a.omega);
     const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
-    const T rs = (a.axis == 1) ? -om * x : T(0);  // rotation symbol factor: -omega x mu (y) ; none for z
+    const T rx = (a.axis == 1) ? -x : T(0);  // rotation symbol -omega x mu (y), omega applied below; none for z
     T akin = 0, arot = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const T k = xia[t + q * Tl];
-      const T mk = T(0.5) * k * k, mr = rs * k;
+      const T mk = T(0.5) * k * k, kr = rx * k;
       const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
-      akin += mk * a2; arot += mr * a2;
-      v[q] = cscale(v[q], (mk + mr) * invM);
+      akin += mk * a2; arot += kr * a2;
+      v[q] = cscale(v[q], (mk + om * kr) * invM);
     }
     line_dft<M, E, +1>(v, sm, si, t, tw);
     C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: final pass writes the caller's buffer

@@ -53,7 +53,8 @@ class GpeError(RuntimeError):
 
 _lib = None
 EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_apply_H_batch", "gpe_precond",
-            "gpe_energy", "gpe_pcg_solve", "gpe_last_error")
+            "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
+            "gpe_pcg_solve", "gpe_last_error")
 
 
 def lib():
@@ -71,6 +72,12 @@ def lib():
         L.gpe_apply_H_batch.argtypes = [vp, C.c_int, vp, vp, vp]
         L.gpe_precond.argtypes = [vp, vp, vp, C.c_double, vp]
         L.gpe_energy.argtypes = [vp, vp, C.POINTER(C.c_double)]
+        L.gpe_set_problem.argtypes = [vp, vp, C.c_double, C.c_double]
+        L.gpe_energy_grad.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_double)]
+        L.gpe_tangent_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double)]
+        L.gpe_density_adjoint.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_double)]
         L.gpe_pcg_solve.argtypes = [vp, vp, C.POINTER(gpe_solve_opts), C.POINTER(gpe_report)]
         L.gpe_last_error.argtypes = [vp]
         L.gpe_last_error.restype = C.c_char_p
@@ -116,6 +123,7 @@ class Context:
             p.L[i] = float(L[i]) if i < len(L) else 1.0
         p.eta, p.omega, p.prec = float(eta), float(omega), int(prec)
         self.n, self.L, self.prec, self.dim = tuple(n), tuple(L), int(prec), len(n)
+        self.eta, self.omega = float(eta), float(omega)
         self._V = V  # keep alive during create
         if isinstance(V, np.ndarray):
             V = np.ascontiguousarray(V, dtype=np.float64)
@@ -146,6 +154,42 @@ class Context:
         self._check(lib().gpe_energy(self._ctx, _addr(phi), out))
         keys = ("kin", "pot", "int", "rot", "total", "lam", "lam_tilde", "norm2")
         return dict(zip(keys, list(out)))
+
+    def set_problem(self, V=None, eta=None, omega=None):
+        """Replace V (float64, host or device; None keeps it), eta and omega (None keeps them)."""
+        Vp = V
+        if isinstance(V, np.ndarray):
+            Vp = np.ascontiguousarray(V, dtype=np.float64)
+        eta = self.eta if eta is None else float(eta)
+        omega = self.omega if omega is None else float(omega)
+        self._check(lib().gpe_set_problem(self._ctx, _addr(Vp), eta, omega))
+        self.eta, self.omega = eta, omega
+
+    def energy_grad(self, phi, grad_phi=None, grad_V=None):
+        """E and its derivatives at phi (gpe_energy_grad); fills grad_phi / grad_V when given."""
+        out = (C.c_double * 5)()
+        self._check(lib().gpe_energy_grad(self._ctx, _addr(phi), _addr(grad_phi), _addr(grad_V), out))
+        keys = ("E", "dE_deta", "dE_domega", "lam", "norm2")
+        return dict(zip(keys, list(out)))
+
+    def tangent_solve(self, phi, rhs, z, tol=1e-10, max_iter=2000, check=True):
+        """gpe_tangent_solve: z with <phi, z> = 0 solving P K z = P rhs.  Returns
+        dict(status, iters, rel_res); raises on failure when check is true."""
+        it, res = C.c_int(0), C.c_double(0.0)
+        s = lib().gpe_tangent_solve(self._ctx, _addr(phi), _addr(rhs), _addr(z), float(tol), int(max_iter),
+                                    C.byref(it), C.byref(res))
+        if check:
+            self._check(s)
+        return dict(status=s, iters=it.value, rel_res=res.value)
+
+    def density_adjoint(self, phi, g_rho, grad_V, tol=1e-10, max_iter=2000, check=True):
+        """gpe_density_adjoint: dL/dV for a loss of |phi*|^2 with cotangent g_rho (float64)."""
+        it, res = C.c_int(0), C.c_double(0.0)
+        s = lib().gpe_density_adjoint(self._ctx, _addr(phi), _addr(g_rho), _addr(grad_V), float(tol), int(max_iter),
+                                      C.byref(it), C.byref(res))
+        if check:
+            self._check(s)
+        return dict(status=s, iters=it.value, rel_res=res.value)
 
     def pcg_solve(self, phi_inout, opts=None, log_cap=0, check=False):
         """Run the solver in place on phi_inout (complex128, host or device).
