@@ -234,15 +234,17 @@ def main():
     value = world * 1000.0 / ms
     launches = 0
     for r in reps:
-        it, lo = r["iters"], r["iters_lo"]
-        if r["loop_kind"] == 3:
-            # conversions (2), normalisations (2), one cluster kernel for the complex64 phase, then the graph
-            launches += 2 + 2 + 1 + 7 * (it - lo + 1)
-        elif r["loop_kind"] == 2:
-            # two precision conversions; per phase one normalisation kernel and one persistent solve kernel
-            launches += 2 + 2 + 2
+        it, lo, fp = r["iters"], r["iters_lo"], r["iters_fp64"]
+        # four precision conversions (c128->c64, c64->c128, c64->ds, ds->c128) and one
+        # normalisation kernel per phase; 7 pass kernels per loop-body execution
+        # (a phase of k iterations executes its body k + 1 times)
+        fp64_phase = (1 + 7 * (fp + 1)) if fp else 0
+        if r["loop_kind"] == 3:  # one cluster kernel runs the complex64 phase
+            launches += 4 + 2 + 1 + 7 * (it - lo - fp + 1) + fp64_phase
+        elif r["loop_kind"] == 2:  # one persistent kernel per phase
+            launches += 4 + 2 + 2 + (2 if fp else 0)
         else:
-            launches += 2 + (1 + 7 * (lo + 1)) + (1 + 7 * (it - lo + 1))
+            launches += 4 + (1 + 7 * (lo + 1)) + (1 + 7 * (it - lo - fp + 1)) + fp64_phase
 
     # ---------------- e2e: phi in pinned host memory ----------------
     phi_h0 = torch.from_numpy(w["phi0"].copy()).pin_memory()
@@ -330,6 +332,7 @@ def main():
             "config": {"workload": WORKLOAD, "grid": "256x256", "domain": "[-16,16]^2", "eta": 1000.0,
                        "omega": 0.9, "V": "r^2/2", "precision": "mixed (c64 phase, c128 refinement)",
                        "tol_res_inf": 1e-8, "iters": last["iters"], "iters_c64": last["iters_lo"],
+                       "iters_fp64": last["iters_fp64"],
                        "loop": {3: "cluster (complex64 phase) + graph (refinement)", 2: "persistent kernel",
                                 1: "graph", 0: "host loop"}[last["loop_kind"]],
                        "loop_note": last.get("note", ""),

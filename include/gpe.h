@@ -99,7 +99,8 @@ typedef struct {
 
 /* Per-iteration log row, doubles: */
 #define GPE_LOG_FIELDS 12
-/* n, phase (0 = complex64, 1 = complex128), E_n, lambda_n, ||r_n||_inf,
+/* n, phase (0 = complex64, 1 = refinement or the FP64 solve, 2 = FP64 completion of a
+ * stalled refinement), E_n, lambda_n, ||r_n||_inf,
  * ||r_n||_2, alpha_n (shift of P_C), beta_n (after max(.,0) and the
  * descent check), theta_n, Delta E_n (accepted step), fallback (1 = gradient
  * step taken), backtracks */
@@ -119,6 +120,8 @@ typedef struct {
   double* log;       /* in: host array [log_cap][GPE_LOG_FIELDS] or NULL */
   int loop_kind;     /* out: loop style that ran (for GPE_MIXED: of the complex64 phase):
                       * 3 cluster, 2 persistent, 1 graph, 0 host loop */
+  int iters_fp64;    /* GPE_MIXED: iterations of the FP64 completion phase (0 unless the
+                      * refinement stalled, see gpe_pcg_solve) */
 } gpe_report;
 
 typedef struct gpe_ctx gpe_ctx;
@@ -249,7 +252,11 @@ gpe_status gpe_density_adjoint(gpe_ctx* ctx, const void* phi_dev, const double* 
  *              not be normalised).  Out: the last iterate phi_n.
  *  opts      : NULL = defaults.
  *  report    : may be NULL.
- * GPE_MIXED runs a complex64 phase, then a complex128 phase from its result.
+ * GPE_MIXED runs a complex64 phase, then a refinement phase from its result
+ * (double-single state and H phi, single-precision direction); if the
+ * refinement's ||r||_inf fails to halve within 4 opts->stall_window iterations
+ * (a near-flat energy direction whose curvature single-precision step
+ * moments cannot resolve), the solve is completed in FP64 from there.
  * Synchronises the stream.  Returns GPE_OK when the stopping rule held, else
  * GPE_ERR_NOT_CONVERGED / GPE_ERR_NONFINITE / GPE_ERR_PRECOND / GPE_ERR_ARG /
  * GPE_ERR_CUDA (report->status carries the same code). */
@@ -283,6 +290,38 @@ gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* op
  * GPE_ERR_CUDA. */
 gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V_dev, const void* phi_dev, const void* f_dev,
                                void* out_dev, void* stream, char* err, size_t err_len);
+
+/* ---- Batched solves ------------------------------------------------------
+ * Many independent ground states (different grids, eta, omega, V; Section 2
+ * problems, each solved by the gpe_pcg_solve algorithm) in ONE graph launch.
+ * The batch holds one context per instance and one CUDA graph with one
+ * branch per instance; the branches run concurrently on the GPU.  A mixed
+ * instance's branch is: the complex64 phase (one thread-block-cluster kernel
+ * for 2D square grids of 32..256 points, else a device-side loop of the pass
+ * kernels), a device-side decision whether to refine, and the refinement
+ * loop; nothing returns to the host until the whole batch is done.  The
+ * paper solves one problem at a time: batching is an interface addition. */
+typedef struct gpe_batch gpe_batch;
+
+/* count instances; probs[i] and V[i] as for gpe_create (V[i] host or device
+ * float64).  stream orders all work.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA (the
+ * message names the instance; read it with gpe_batch_last_error(NULL)). */
+gpe_status gpe_batch_create(int count, const gpe_problem* probs, const double* const* V, void* stream,
+                            gpe_batch** out);
+
+/* Solve every instance from phi_inout[i] (complex128, host or device; in:
+ * initial guess, out: last iterate), with the same options for all (NULL =
+ * defaults; refine_restart, use_graph and the log are ignored: the batch always
+ * restarts beta at the refinement and keeps no log).  reports: NULL or an
+ * array of count reports.  The graph is built by the first call.  Synchronises
+ * the stream.  Returns GPE_OK when every instance met the stopping rule, else
+ * the first failing instance's status (each report carries its own). */
+gpe_status gpe_batch_solve(gpe_batch* batch, void* const* phi_inout, const gpe_solve_opts* opts, gpe_report* reports);
+
+gpe_status gpe_batch_destroy(gpe_batch* batch);
+
+/* Last failure on batch ("" if none); NULL: the last failed gpe_batch_create. */
+const char* gpe_batch_last_error(const gpe_batch* batch);
 
 /* Human-readable description of the last failure on ctx ("" if none).
  * The string is owned by ctx and valid until its next call. ctx NULL gives

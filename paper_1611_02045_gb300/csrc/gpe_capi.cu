@@ -817,7 +817,7 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
     if (s != GPE_OK) return s;
     if (done_launch) loop = 2;
   }
-  if (mode != 2) c->last_loop = loop;  // a mixed solve reports its complex64 phase's loop
+  if (mode == 0 || c->prob.prec != GPE_MIXED) c->last_loop = loop;  // a mixed solve reports its complex64 phase's loop
   if (done_launch) {
   } else if (o.use_graph) {
     s = build_graph(c, mode);
@@ -841,17 +841,41 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
   return GPE_OK;
 }
 
+// Control block at the start of a solve (options, loop state, the
+// single-precision floor estimate used by the complex64 phase's switch rule).
+static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
+  Ctl h;
+  std::memset(&h, 0, sizeof(h));
+  h.tol_res_inf = o.tol_res_inf; h.tol_dE = o.tol_dE; h.theta_default = o.theta_default; h.switch_res = o.switch_res;
+  h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
+  h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
+  h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
+  double k2 = 0.0;  // max over the grid of |k|^2 / 2 (corner mode -M/2 on every axis)
+  for (int i = 0; i < c->dim; ++i) {
+    const double km = 0.5 * c->n[i] * M_PI / c->prob.L[i];
+    k2 += 0.5 * km * km;
+  }
+  h.floor_coef = 5.96e-8 * (k2 + (c->vmax > 0.0 ? c->vmax : 0.0));
+  h.switch_fac = 4.0;
+  return h;
+}
+
+static gpe_status check_opts(gpe_solve_opts& o, std::string& err) {
+  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1) {
+    err = "invalid solve options";
+    return GPE_ERR_ARG;
+  }
+  if (o.max_iter_lo <= 0) o.max_iter_lo = o.max_iter;
+  return GPE_OK;
+}
+
 extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve_opts* opts, gpe_report* rep) {
   if (!c) return GPE_ERR_ARG;
   if (!phi_inout) { c->err = "null phi"; return GPE_ERR_ARG; }
   gpe_solve_opts o;
   gpe_solve_opts_default(&o);
   if (opts) o = *opts;
-  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1) {
-    c->err = "invalid solve options";
-    return GPE_ERR_ARG;
-  }
-  if (o.max_iter_lo <= 0) o.max_iter_lo = o.max_iter;
+  if (check_opts(o, c->err) != GPE_OK) return GPE_ERR_ARG;
   const int log_cap = (rep && rep->log && rep->log_cap > 0) ? rep->log_cap : 0;
   if (log_cap > c->log_dev_cap) {
     cudaFree(c->log_dev);
@@ -864,23 +888,8 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
   const size_t b128 = 16 * (size_t)c->N;
   GPE_CU(c, cudaMemcpyAsync(c->pb[1].phi, phi_inout, b128, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
 
-  Ctl h;
-  std::memset(&h, 0, sizeof(h));
-  h.tol_res_inf = o.tol_res_inf; h.tol_dE = o.tol_dE; h.theta_default = o.theta_default; h.switch_res = o.switch_res;
-  h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
-  h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
-  h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
-  {
-    double k2 = 0.0;  // max over the grid of |k|^2 / 2 (corner mode -M/2 on every axis)
-    for (int i = 0; i < c->dim; ++i) {
-      const double km = 0.5 * c->n[i] * M_PI / c->prob.L[i];
-      k2 += 0.5 * km * km;
-    }
-    h.floor_coef = 5.96e-8 * (k2 + (c->vmax > 0.0 ? c->vmax : 0.0));
-    h.switch_fac = 4.0;
-  }
-
-  int iters_lo = 0;
+  Ctl h = solve_ctl(c, o, log_cap);
+  int iters_lo = 0, iters_hi = 0;
   gpe_status s;
   if (c->prob.prec == GPE_MIXED) {
     GPE_CU(c, launch_convert_c128_to_c64(c->pb[1].phi, c->pb[0].phi, c->N, c->st));
@@ -901,6 +910,7 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
       h.done = 0; h.status = 0; h.switch_req = 0; h.lo_phase = 0; h.phase = 1; h.restart = keep ? 0 : 1;
       h.stop_dE = 0;
       h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter;
+      h.stall_switch = 1; h.anchor_res = 1e300; h.anchor_iter = h.iter;
       // the refinement state lives in double-single: phi (and, when the
       // direction is kept, r_{n-1}; p is complex64 in both phases)
       GPE_CU(c, launch_convert_c64_to_ds(c->pb[0].phi, c->pb[2].phi, c->N, c->st));
@@ -909,6 +919,14 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
       if (s != GPE_OK) return s;
       if (h.status != GPE_ERR_NONFINITE && h.status != GPE_ERR_PRECOND)
         GPE_CU(c, launch_convert_ds_to_c128(c->pb[2].phi, c->pb[1].phi, c->N, c->st));
+      if (h.switch_req && h.stall_switch && h.iter < o.max_iter) {
+        // the refinement stalled: complete the solve in FP64 from its last iterate
+        iters_hi = h.iter;
+        h.done = 0; h.status = 0; h.switch_req = 0; h.phase = 2; h.restart = 1; h.stop_dE = 0;
+        h.iter_phase0 = h.iter; h.max_iter_phase = o.max_iter; h.stall_switch = 0;
+        s = run_phase(c, 1, h, o);
+        if (s != GPE_OK) return s;
+      }
     }
   } else {
     h.lo_phase = 0; h.phase = 1; h.max_iter_phase = o.max_iter;
@@ -922,6 +940,7 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
     rep->fallbacks = h.fallbacks; rep->backtracks = h.backtracks_total;
     rep->E = h.E; rep->lambda = h.lam; rep->res_inf = h.res_inf; rep->res_l2 = h.res_l2;
     rep->loop_kind = c->last_loop;
+    rep->iters_fp64 = iters_hi ? h.iter - iters_hi : 0;
     rep->log_len = 0;
     if (log_cap) {
       int nrows = h.iter + 1 < log_cap ? h.iter + 1 : log_cap;
@@ -937,3 +956,247 @@ extern "C" gpe_status gpe_pcg_solve(gpe_ctx* c, void* phi_inout, const gpe_solve
   }
   return (gpe_status)h.status;
 }
+
+// ---------------------------------------------------------------------------
+// Batched solves: one CUDA graph with one branch per instance
+// ---------------------------------------------------------------------------
+struct gpe_batch {
+  std::vector<gpe_ctx*> ctx;
+  std::vector<Ctl*> ctl_init;  // device copies of each solve's starting control block
+  cudaStream_t st = nullptr;    // caller's stream
+  cudaStream_t cap = nullptr;   // capture of the branches
+  cudaStream_t body = nullptr;  // capture of the loop bodies
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+};
+
+static bool cluster_eligible(const gpe_ctx* c) {
+  return c->dim == 2 && c->n[0] == c->n[1] && c->n[0] >= 32 && c->n[0] <= 256;
+}
+
+// Append a WHILE node after the nodes captured so far on st; its body, one
+// iteration of launch mode `mode` whose last pass re-arms h, is captured on body_st.
+static gpe_status capture_while(gpe_batch* B, gpe_ctx* c, int mode, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  GPE_CU(B, cudaStreamGetCaptureInfo(B->cap, &cs, nullptr, &graph, &deps, &ed, &nd));
+  if (cs != cudaStreamCaptureStatusActive) { B->err = "batch capture is not active"; return GPE_ERR_CUDA; }
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  GPE_CU(B, cudaGraphAddNode(&node, graph, deps, ed, nd, &np));
+  GPE_CU(B, cudaStreamUpdateCaptureDependencies(B->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  GPE_CU(B, cudaStreamBeginCaptureToGraph(B->body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+  gpe_status s = enqueue_iteration(c, mode, B->body, (unsigned long long)h);
+  cudaGraph_t got = nullptr;
+  cudaError_t e = cudaStreamEndCapture(B->body, &got);
+  if (s != GPE_OK) { B->err = c->err; return s; }
+  if (e != cudaSuccess) { B->err = std::string("loop body capture: ") + cudaGetErrorString(e); return GPE_ERR_CUDA; }
+  return GPE_OK;
+}
+
+static gpe_status new_handle(gpe_batch* B, unsigned dflt, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  GPE_CU(B, cudaStreamGetCaptureInfo(B->cap, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+  GPE_CU(B, cudaGraphConditionalHandleCreate(h, graph, dflt, cudaGraphCondAssignDefault));
+  return GPE_OK;
+}
+
+// One instance's whole solve, captured on B->cap: the steps of gpe_pcg_solve
+// with the host's decisions between the phases taken by batch kernels.
+static gpe_status batch_enqueue(gpe_batch* B, gpe_ctx* c, Ctl* ctl_init) {
+  cudaStream_t st = B->cap;
+  const long long N = c->N;
+  gpe_status s;
+  GPE_CU(B, cudaMemcpyAsync(c->ctl_solve, ctl_init, sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  auto clear_dir = [&](const IterBufs& b) -> gpe_status {
+    GPE_CU(B, cudaMemsetAsync(b.p, 0, (b.tab_d ? 16 : 8) * (size_t)N, st));
+    GPE_CU(B, cudaMemsetAsync(b.r_prev, 0, (b.tab_h ? 16 : 8) * (size_t)N, st));
+    return GPE_OK;
+  };
+  if (c->prob.prec != GPE_MIXED) {
+    const IterBufs b1 = iter_bufs(c, 1);
+    if ((s = clear_dir(b1)) != GPE_OK) return s;
+    GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, st));
+    cudaGraphConditionalHandle h;
+    if ((s = new_handle(B, 1, &h)) != GPE_OK) return s;
+    return capture_while(B, c, 1, h);
+  }
+  const IterBufs b0 = iter_bufs(c, 0);
+  GPE_CU(B, launch_convert_c128_to_c64(c->pb[1].phi, c->pb[0].phi, N, st));
+  if ((s = clear_dir(b0)) != GPE_OK) return s;
+  GPE_CU(B, launch_init_norm(b0.tab_h, b0.phi, N, c->weight, c->ctl_solve, st));
+  if (cluster_eligible(c)) {
+    ClusterSolveArgs P;
+    std::memset(&P, 0, sizeof(P));
+    P.base = iter_args(c, 0, 0ull).hx;
+    P.phi = static_cast<float2*>(b0.phi);
+    P.V = static_cast<const float*>(b0.V);
+    P.ctl = c->ctl_solve;
+    GPE_CU(B, launch_cluster_solve(c->n[0], P, st));
+  } else {
+    cudaGraphConditionalHandle h0;
+    if ((s = new_handle(B, 1, &h0)) != GPE_OK) return s;
+    if ((s = capture_while(B, c, 0, h0)) != GPE_OK) return s;
+  }
+  const IterBufs b2 = iter_bufs(c, 2);
+  GPE_CU(B, launch_batch_between(c->pb[0].phi, c->pb[1].phi, c->pb[2].phi, N, c->ctl_solve, st));
+  if ((s = clear_dir(b2)) != GPE_OK) return s;
+  GPE_CU(B, launch_init_norm(b2.tab_h, b2.phi, N, c->weight, c->ctl_solve, st));
+  cudaGraphConditionalHandle h2;
+  if ((s = new_handle(B, 0, &h2)) != GPE_OK) return s;
+  GPE_CU(B, launch_batch_gate(c->ctl_solve, (unsigned long long)h2, st));
+  if ((s = capture_while(B, c, 2, h2)) != GPE_OK) return s;
+  GPE_CU(B, launch_batch_final(c->pb[2].phi, c->pb[1].phi, N, c->ctl_solve, st));
+  // FP64 completion when the refinement stalled
+  const IterBufs b1 = iter_bufs(c, 1);
+  if ((s = clear_dir(b1)) != GPE_OK) return s;
+  GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, st));
+  cudaGraphConditionalHandle h3;
+  if ((s = new_handle(B, 0, &h3)) != GPE_OK) return s;
+  GPE_CU(B, launch_batch_gate64(c->ctl_solve, (unsigned long long)h3, st));
+  return capture_while(B, c, 1, h3);
+}
+
+static gpe_status batch_build(gpe_batch* B) {
+  if (B->exec) return GPE_OK;
+  for (gpe_ctx* c : B->ctx) {  // kernel attributes are set outside capture
+    gpe_status s = GPE_OK;
+    if (c->prob.prec == GPE_MIXED) {
+      if ((s = warm_kernels(c, 0)) == GPE_OK) s = warm_kernels(c, 2);
+      if (s == GPE_OK) s = warm_kernels(c, 1);
+      if (s == GPE_OK && cluster_eligible(c)) GPE_CU(B, prepare_cluster_solve(c->n[0]));
+    } else {
+      s = warm_kernels(c, 1);
+    }
+    if (s != GPE_OK) { B->err = c->err; return s; }
+  }
+  cudaGraph_t g = nullptr;
+  GPE_CU(B, cudaGraphCreate(&g, 0));
+  for (size_t i = 0; i < B->ctx.size(); ++i) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(B->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { B->err = std::string("batch capture: ") + cudaGetErrorString(e); cudaGraphDestroy(g); return GPE_ERR_CUDA; }
+    gpe_status s = batch_enqueue(B, B->ctx[i], B->ctl_init[i]);
+    cudaGraph_t got = nullptr;
+    e = cudaStreamEndCapture(B->cap, &got);
+    if (s != GPE_OK) { cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) { B->err = std::string("batch capture: ") + cudaGetErrorString(e); cudaGraphDestroy(g); return GPE_ERR_CUDA; }
+  }
+  cudaError_t e = cudaGraphInstantiate(&B->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { B->exec = nullptr; B->err = std::string("batch instantiate: ") + cudaGetErrorString(e); return GPE_ERR_CUDA; }
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_batch_destroy(gpe_batch* B) {
+  if (!B) return GPE_OK;
+  if (B->st) cudaStreamSynchronize(B->st);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (Ctl* p : B->ctl_init) cudaFree(p);
+  for (gpe_ctx* c : B->ctx) gpe_destroy(c);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->body) cudaStreamDestroy(B->body);
+  delete B;
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_batch_create(int count, const gpe_problem* probs, const double* const* V, void* stream,
+                                       gpe_batch** out) {
+  if (!out) { g_create_error = "null argument"; return GPE_ERR_ARG; }
+  *out = nullptr;
+  if (count < 1 || !probs || !V) { g_create_error = "count >= 1, probs and V required"; return GPE_ERR_ARG; }
+  gpe_batch* B = new gpe_batch();
+  B->st = (cudaStream_t)stream;
+  auto fail = [&](gpe_status s, const std::string& msg) {
+    g_create_error = msg;
+    gpe_batch_destroy(B);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&B->body, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(GPE_ERR_CUDA, "stream create failed");
+  for (int i = 0; i < count; ++i) {
+    gpe_ctx* c = nullptr;
+    gpe_status s = gpe_create(&probs[i], V[i], stream, &c);
+    if (s != GPE_OK) return fail(s, "instance " + std::to_string(i) + ": " + g_create_error);
+    B->ctx.push_back(c);
+    Ctl* p = nullptr;
+    if (cudaMalloc(&p, sizeof(Ctl)) != cudaSuccess) return fail(GPE_ERR_CUDA, "cudaMalloc control block");
+    B->ctl_init.push_back(p);
+  }
+  *out = B;
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_batch_solve(gpe_batch* B, void* const* phi_inout, const gpe_solve_opts* opts,
+                                      gpe_report* reports) {
+  if (!B) return GPE_ERR_ARG;
+  if (!phi_inout) { B->err = "null phi array"; return GPE_ERR_ARG; }
+  gpe_solve_opts o;
+  gpe_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (check_opts(o, B->err) != GPE_OK) return GPE_ERR_ARG;
+  const size_t n = B->ctx.size();
+  for (size_t i = 0; i < n; ++i)
+    if (!phi_inout[i]) { B->err = "null phi for instance " + std::to_string(i); return GPE_ERR_ARG; }
+  std::vector<Ctl> init(n), fin(n);
+  std::vector<char> on_dev(n);
+  for (size_t i = 0; i < n; ++i) {
+    gpe_ctx* c = B->ctx[i];
+    init[i] = solve_ctl(c, o, 0);
+    if (c->prob.prec == GPE_MIXED) {
+      init[i].lo_phase = 1; init[i].phase = 0; init[i].max_iter_phase = o.max_iter_lo;
+    } else {
+      init[i].lo_phase = 0; init[i].phase = 1; init[i].max_iter_phase = o.max_iter;
+    }
+    on_dev[i] = is_device_ptr(phi_inout[i]);
+    GPE_CU(B, cudaMemcpyAsync(B->ctl_init[i], &init[i], sizeof(Ctl), cudaMemcpyHostToDevice, B->st));
+    GPE_CU(B, cudaMemcpyAsync(c->pb[1].phi, phi_inout[i], 16 * (size_t)c->N,
+                              on_dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->st));
+  }
+  GPE_CU(B, cudaStreamSynchronize(B->st));
+  gpe_status s = batch_build(B);
+  if (s != GPE_OK) return s;
+  GPE_CU(B, cudaGraphLaunch(B->exec, B->st));
+  for (size_t i = 0; i < n; ++i) {
+    gpe_ctx* c = B->ctx[i];
+    GPE_CU(B, cudaMemcpyAsync(phi_inout[i], c->pb[1].phi, 16 * (size_t)c->N,
+                              on_dev[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, B->st));
+    GPE_CU(B, cudaMemcpyAsync(&fin[i], c->ctl_solve, sizeof(Ctl), cudaMemcpyDeviceToHost, B->st));
+  }
+  GPE_CU(B, cudaStreamSynchronize(B->st));
+  int failed = 0, first_bad = GPE_OK;
+  for (size_t i = 0; i < n; ++i) {
+    const Ctl& h = fin[i];
+    if (h.status != GPE_OK) {
+      ++failed;
+      if (first_bad == GPE_OK) first_bad = h.status;
+    }
+    if (reports) {
+      gpe_report& r = reports[i];
+      r.status = h.status; r.iters = h.iter;
+      r.iters_lo = B->ctx[i]->prob.prec == GPE_MIXED ? h.iters_lo : 0;
+      r.iters_fp64 = h.iters_hi ? h.iter - h.iters_hi : 0;
+      r.fallbacks = h.fallbacks; r.backtracks = h.backtracks_total;
+      r.E = h.E; r.lambda = h.lam; r.res_inf = h.res_inf; r.res_l2 = h.res_l2;
+      r.log_len = 0;
+      r.loop_kind = (B->ctx[i]->prob.prec == GPE_MIXED && cluster_eligible(B->ctx[i])) ? 3 : 1;
+    }
+  }
+  if (failed) {
+    B->err = std::to_string(failed) + " of " + std::to_string(n) + " solves did not meet the stopping rule";
+    return (gpe_status)first_bad;
+  }
+  B->err.clear();
+  return GPE_OK;
+}
+
+extern "C" const char* gpe_batch_last_error(const gpe_batch* B) { return B ? B->err.c_str() : g_create_error.c_str(); }
+

@@ -23,6 +23,16 @@ cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStr
   }
 }
 
+cudaError_t prepare_cluster_solve(int M) {
+  switch (M) {
+    case 32: return cluster_solve_attrs<32>();
+    case 64: return cluster_solve_attrs<64>();
+    case 128: return cluster_solve_attrs<128>();
+    case 256: return cluster_solve_attrs<256>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_cluster_solve(int M, const ClusterSolveArgs& P, cudaStream_t st) {
   switch (M) {
     case 32: return launch_cluster_solve_one<32>(P, st);

@@ -251,22 +251,36 @@ __global__ void __launch_bounds__((M / 8) * kCSRows) cluster_solve(ClusterSolveA
 }
 
 template <int M>
+constexpr size_t cluster_solve_smem() {
+  return (size_t)(5 * kCSRows * M + kCSRows * (M + M / 16)) * sizeof(float2);
+}
+
+// Kernel attributes (dynamic shared memory, non-portable cluster size), set
+// once; call before any stream capture that launches the kernel.
+template <int M>
+cudaError_t cluster_solve_attrs() {
+  static bool attr = false;
+  if (attr) return cudaSuccess;
+  auto kern = cluster_solve<M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_solve_smem<M>());
+  if (e != cudaSuccess) return e;
+  if (M / kCSRows > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  attr = true;
+  return cudaSuccess;
+}
+
+template <int M>
 cudaError_t launch_cluster_solve_one(const ClusterSolveArgs& P, cudaStream_t st) {
   constexpr int R = kCSRows;
   const int csize = M / R;
   const int threads = (M / 8) * R;
-  const size_t smem = (size_t)(5 * R * M + R * (M + M / 16)) * sizeof(float2);
+  const size_t smem = cluster_solve_smem<M>();
   auto kern = cluster_solve<M>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (csize > 8) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-    }
-    attr = true;
-  }
+  cudaError_t e = cluster_solve_attrs<M>();
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)csize);
   cfg.blockDim = dim3((unsigned)threads);

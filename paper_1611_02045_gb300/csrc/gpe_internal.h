@@ -22,6 +22,10 @@ struct Ctl {
   // ---- loop state ----
   int iter;        // n (global over both phases)
   int iter_phase0; // value of iter when this phase started
+  int iters_lo;    // batched mixed solve: iterations of the complex64 phase
+  int iters_hi;    // batched mixed solve: iteration count when the FP64 completion phase started (0: none)
+  int stall_switch;  // 1 in the refinement phase: a stall (no halving of ||r||_inf in stall_window
+                     // iterations) ends it with switch_req, and the solve is completed in FP64
   int done;        // 1 once the loop must stop
   int status;      // gpe_status of the solve
   int restart;     // 1: next direction uses beta = 0 (first iteration of a phase)
@@ -170,6 +174,25 @@ cudaError_t adj_density_rhs(int prec, const void* phi, const double* g_rho, void
                             cudaStream_t st);
 cudaError_t adj_dV_from_z(int prec, const void* phi, const void* z, double* gV, long long n, double weight,
                           cudaStream_t st);
+
+// Between the phases of a batched mixed solve (the host logic of
+// gpe_pcg_solve, on the device so that a whole batch is one graph):
+//  batch_between: unless the complex64 phase failed (non-finite, P_V
+//    undefined), phi128 = phi64 and phids = phi64;
+//  batch_gate (one thread): records iters_lo; if the complex64 phase asked for
+//    refinement (or "converged" in single precision) and iterations remain,
+//    re-arms ctl for the refinement phase (beta restart) and sets the
+//    refinement loop's condition to 1, else to 0;
+//  batch_final: if the refinement ran and did not fail, phi128 = phids.
+cudaError_t launch_batch_between(const void* phi64, void* phi128, void* phids, long long n, const Ctl* ctl,
+                                 cudaStream_t st);
+cudaError_t launch_batch_gate(Ctl* ctl, unsigned long long cond, cudaStream_t st);
+cudaError_t launch_batch_final(const void* phids, void* phi128, long long n, const Ctl* ctl, cudaStream_t st);
+//  batch_gate64 (one thread): if the refinement stalled and iterations remain,
+//    re-arms ctl for the FP64 completion phase and sets its loop condition.
+cudaError_t launch_batch_gate64(Ctl* ctl, unsigned long long cond, cudaStream_t st);
+// Set the cluster solve kernel's attributes for grid size M (before capture).
+cudaError_t prepare_cluster_solve(int M);
 
 // grad_phi <- 2 weight grad_phi (in place), grad_V = weight |phi|^2 (float64);
 // prec 0 complex64, 1 complex128; null outputs are skipped.

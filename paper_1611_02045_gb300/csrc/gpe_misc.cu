@@ -132,6 +132,72 @@ cudaError_t launch_grad_epilogue(int prec, const void* phi, void* gphi, double* 
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ bool phase_failed(int status) { return status == 4 || status == 5; }  // non-finite, P_V
+
+__global__ void k_batch_between(const float2* __restrict__ s, double2* __restrict__ d128, dsc* __restrict__ dds,
+                                long long n, const Ctl* __restrict__ ctl) {
+  if (phase_failed(ctl->status)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = s[i];
+    d128[i] = make_double2((double)v.x, (double)v.y);
+    dsc w;
+    w.x = dsf(v.x);
+    w.y = dsf(v.y);
+    dds[i] = w;
+  }
+}
+cudaError_t launch_batch_between(const void* phi64, void* phi128, void* phids, long long n, const Ctl* ctl,
+                                 cudaStream_t st) {
+  k_batch_between<<<grid_for(n), 256, 0, st>>>((const float2*)phi64, (double2*)phi128, (dsc*)phids, n, ctl);
+  return cudaGetLastError();
+}
+
+__global__ void k_batch_gate(Ctl* ctl, cudaGraphConditionalHandle cond) {
+  Ctl& c = *ctl;
+  c.iters_lo = c.iter;
+  const bool go_on = (c.switch_req || c.status == 0) && !phase_failed(c.status);
+  unsigned refine = 0;
+  if (go_on && c.iter < c.max_iter) {
+    c.done = 0; c.status = 0; c.switch_req = 0; c.lo_phase = 0; c.phase = 1; c.restart = 1; c.stop_dE = 0;
+    c.iter_phase0 = c.iter; c.max_iter_phase = c.max_iter;
+    c.stall_switch = 1; c.anchor_res = 1e300; c.anchor_iter = c.iter;
+    refine = 1;
+  }
+  cudaGraphSetConditional(cond, refine);
+}
+
+__global__ void k_batch_gate64(Ctl* ctl, cudaGraphConditionalHandle cond) {
+  Ctl& c = *ctl;
+  unsigned run = 0;
+  if (c.phase == 1 && c.lo_phase == 0 && c.stall_switch && c.switch_req && c.iter < c.max_iter) {
+    c.iters_hi = c.iter;
+    c.done = 0; c.status = 0; c.switch_req = 0; c.phase = 2; c.restart = 1; c.stop_dE = 0;
+    c.iter_phase0 = c.iter; c.max_iter_phase = c.max_iter; c.stall_switch = 0;
+    run = 1;
+  }
+  cudaGraphSetConditional(cond, run);
+}
+cudaError_t launch_batch_gate64(Ctl* ctl, unsigned long long cond, cudaStream_t st) {
+  k_batch_gate64<<<1, 1, 0, st>>>(ctl, (cudaGraphConditionalHandle)cond);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_gate(Ctl* ctl, unsigned long long cond, cudaStream_t st) {
+  k_batch_gate<<<1, 1, 0, st>>>(ctl, (cudaGraphConditionalHandle)cond);
+  return cudaGetLastError();
+}
+
+__global__ void k_batch_final(const dsc* __restrict__ s, double2* __restrict__ d, long long n, const Ctl* __restrict__ ctl) {
+  if (ctl->phase != 1 || ctl->lo_phase != 0 || phase_failed(ctl->status)) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dsc v = s[i];
+    d[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+cudaError_t launch_batch_final(const void* phids, void* phi128, long long n, const Ctl* ctl, cudaStream_t st) {
+  k_batch_final<<<grid_for(n), 256, 0, st>>>((const dsc*)phids, (double2*)phi128, n, ctl);
+  return cudaGetLastError();
+}
+
 // One block, fixed-order FP64 sum of |phi|^2 (runs once per solve phase).
 template <typename C>
 __global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, long long n, double weight, Ctl* ctl) {

@@ -240,6 +240,15 @@ static __device__ void finalize_C1(Ctl* c, const Fin& a, const double (&tot)[3],
     if (c->res_inf < thr || stalled || nphase >= c->max_iter_phase) {
       c->switch_req = 1; c->status = ST_NOT_CONVERGED; c->done = 1;
     }
+  } else if (c->stall_switch) {
+    // refinement phase: its step moments are single precision; if ||r||_inf
+    // has not halved for 4 stall_window iterations, finish in FP64 (after the
+    // beta restart ||r||_inf first grows ~10x; on the 256^2 and 128^3 bench
+    // problems the longest gap between halvings is ~1500 iterations)
+    if (c->res_inf <= 0.5 * c->anchor_res) { c->anchor_res = c->res_inf; c->anchor_iter = c->iter; }
+    if (c->iter - c->anchor_iter >= 4 * c->stall_window) {
+      c->switch_req = 1; c->status = ST_NOT_CONVERGED; c->done = 1;
+    }
   }
 }
 

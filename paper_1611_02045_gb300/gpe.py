@@ -42,7 +42,7 @@ class gpe_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("iters_lo", C.c_int), ("fallbacks", C.c_int),
                 ("backtracks", C.c_int), ("E", C.c_double), ("lambda_", C.c_double), ("res_inf", C.c_double),
                 ("res_l2", C.c_double), ("log_cap", C.c_int), ("log_len", C.c_int),
-                ("log", C.POINTER(C.c_double)), ("loop_kind", C.c_int)]
+                ("log", C.POINTER(C.c_double)), ("loop_kind", C.c_int), ("iters_fp64", C.c_int)]
 
 
 class GpeError(RuntimeError):
@@ -54,7 +54,9 @@ class GpeError(RuntimeError):
 _lib = None
 EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_apply_H_batch", "gpe_precond",
             "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
-            "gpe_pcg_solve", "gpe_last_error")
+            "gpe_pcg_solve", "gpe_last_error", "gpe_batch_create", "gpe_batch_solve", "gpe_batch_destroy",
+            "gpe_batch_last_error")
+_STRING_RETURNING = ("gpe_last_error", "gpe_batch_last_error")
 
 
 def lib():
@@ -81,8 +83,13 @@ def lib():
         L.gpe_pcg_solve.argtypes = [vp, vp, C.POINTER(gpe_solve_opts), C.POINTER(gpe_report)]
         L.gpe_last_error.argtypes = [vp]
         L.gpe_last_error.restype = C.c_char_p
+        L.gpe_batch_create.argtypes = [C.c_int, C.POINTER(gpe_problem), C.POINTER(vp), vp, C.POINTER(vp)]
+        L.gpe_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(gpe_solve_opts), C.POINTER(gpe_report)]
+        L.gpe_batch_destroy.argtypes = [vp]
+        L.gpe_batch_last_error.argtypes = [vp]
+        L.gpe_batch_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name != "gpe_last_error":
+            if name not in _STRING_RETURNING:
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -208,7 +215,7 @@ class Context:
         out = dict(status=rep.status, status_name=STATUS_NAMES.get(rep.status), iters=rep.iters,
                    iters_lo=rep.iters_lo, fallbacks=rep.fallbacks, backtracks=rep.backtracks, E=rep.E,
                    lam=rep.lambda_, res_inf=rep.res_inf, res_l2=rep.res_l2, loop_kind=rep.loop_kind,
-                   note=lib().gpe_last_error(self._ctx).decode())
+                   iters_fp64=rep.iters_fp64, note=lib().gpe_last_error(self._ctx).decode())
         if logbuf is not None:
             out["log"] = logbuf[: rep.log_len].copy()
         return out
@@ -217,6 +224,79 @@ class Context:
         if getattr(self, "_ctx", None):
             lib().gpe_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _problem(n, L, eta, omega, prec):
+    p = gpe_problem()
+    p.dim = len(n)
+    for i in range(3):
+        p.n[i] = int(n[i]) if i < len(n) else 1
+        p.L[i] = float(L[i]) if i < len(L) else 1.0
+    p.eta, p.omega, p.prec = float(eta), float(omega), int(prec)
+    return p
+
+
+class Batch:
+    """Owns one gpe_batch: many independent solves in one graph launch.
+
+    instances: sequence of dicts with n, L, eta, omega, V (float64 host array or
+    device tensor) and optionally prec (default GPE_MIXED)."""
+
+    def __init__(self, instances, stream=None):
+        L_ = lib()
+        cnt = len(instances)
+        probs = (gpe_problem * cnt)()
+        Vs = (C.c_void_p * cnt)()
+        self._keep = []
+        for i, w in enumerate(instances):
+            probs[i] = _problem(w["n"], w["L"], w["eta"], w["omega"], w.get("prec", GPE_MIXED))
+            V = w["V"]
+            if isinstance(V, np.ndarray):
+                V = np.ascontiguousarray(V, dtype=np.float64)
+            self._keep.append(V)
+            Vs[i] = _addr(V)
+        b = C.c_void_p()
+        s = L_.gpe_batch_create(cnt, probs, Vs, _stream_handle(stream), C.byref(b))
+        self._keep = None
+        if s != GPE_OK:
+            raise GpeError(s, L_.gpe_batch_last_error(None).decode())
+        self._b = b
+        self.count = cnt
+
+    def solve(self, phis, opts=None, check=False):
+        """Solve all instances in place (phis: complex128 tensors/arrays, one per
+        instance).  Returns (status, list of per-instance report dicts)."""
+        if len(phis) != self.count:
+            raise ValueError("one initial guess per instance")
+        if opts is None:
+            opts = solve_opts_default()
+        ptrs = (C.c_void_p * self.count)(*[_addr(p) for p in phis])
+        reps = (gpe_report * self.count)()
+        s = lib().gpe_batch_solve(self._b, ptrs, C.byref(opts), reps)
+        msg = lib().gpe_batch_last_error(self._b).decode()
+        if s in (GPE_ERR_ARG, GPE_ERR_CUDA) or (check and s != GPE_OK):
+            raise GpeError(s, msg)
+        out = [dict(status=r.status, status_name=STATUS_NAMES.get(r.status), iters=r.iters, iters_lo=r.iters_lo,
+                    fallbacks=r.fallbacks, backtracks=r.backtracks, E=r.E, lam=r.lambda_, res_inf=r.res_inf,
+                    res_l2=r.res_l2, loop_kind=r.loop_kind, iters_fp64=r.iters_fp64) for r in reps]
+        return s, out
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().gpe_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

@@ -182,3 +182,37 @@ def workload(name: str, index: int = 0):
         phi0 = perturbed(phi_d(n, L, 0.7), 70 + index, n, L)
         return dict(n=n, L=L, eta=500.0, omega=0.7, V=V, phi0=phi0)
     raise KeyError(name)
+
+
+def sweep_instances(count: int = 96, seed: int = 3, grids=(128, 256, 512)):
+    """The batched parameter sweep: `count` independent 2D problems on
+    [-16,16]^2 (count a multiple of len(grids); equally many of each grid size,
+    in a seeded order), omega ~ U[0, 0.95], eta in {100, 250, 500, 1000},
+    V = r^2/2 + kappa r^4/4 with kappa in {0, 0.05}, initial guess phi_d(omega)
+    with a 1e-3 perturbation (seed 100 + i).  Parameters are drawn from
+    splitmix64 with `seed`: per instance i, uniforms u[4i..4i+3] give omega,
+    the eta index, kappa and the grid-order key.  Returns a list of dicts
+    (n, L, eta, omega, kappa, V, phi0); V and phi0 are built on demand by
+    sweep_arrays()."""
+    if count % len(grids):
+        raise ValueError("count must be a multiple of the number of grid sizes")
+    u = uniform_pm1(seed, 4 * count).reshape(count, 4)
+    base = np.repeat(np.asarray(grids), count // len(grids))
+    order = np.argsort(u[:, 3], kind="stable")
+    sizes = base[np.argsort(order, kind="stable")]
+    etas = (100.0, 250.0, 500.0, 1000.0)
+    out = []
+    for i in range(count):
+        M = int(sizes[i])
+        out.append(dict(n=(M, M), L=(16.0, 16.0), omega=0.95 * 0.5 * (u[i, 0] + 1.0),
+                        eta=etas[min(int(2.0 * (u[i, 1] + 1.0)), 3)],
+                        kappa=0.05 if u[i, 2] > 0.0 else 0.0, seed=100 + i))
+    return out
+
+
+def sweep_arrays(inst):
+    """(V, phi0) of one sweep instance."""
+    n, L = inst["n"], inst["L"]
+    V = harmonic_quartic(n, L, inst["kappa"])
+    phi0 = perturbed(phi_d(n, L, inst["omega"]), inst["seed"], n, L)
+    return V, phi0

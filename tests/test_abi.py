@@ -45,8 +45,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(gpe_problem), offsetof(gpe_problem, eta), offsetof(gpe_problem, prec));
   printf("%zu %zu %zu %zu\n", sizeof(gpe_solve_opts), offsetof(gpe_solve_opts, switch_res), offsetof(gpe_solve_opts, use_graph),
          offsetof(gpe_solve_opts, refine_restart));
-  printf("%zu %zu %zu %zu\n", sizeof(gpe_report), offsetof(gpe_report, res_l2), offsetof(gpe_report, log),
-         offsetof(gpe_report, loop_kind));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(gpe_report), offsetof(gpe_report, res_l2), offsetof(gpe_report, log),
+         offsetof(gpe_report, loop_kind), offsetof(gpe_report, iters_fp64));
   return 0;
 }
 """
@@ -61,7 +61,7 @@ int main(void) {
             C.sizeof(G.gpe_solve_opts), G.gpe_solve_opts.switch_res.offset, G.gpe_solve_opts.use_graph.offset,
             G.gpe_solve_opts.refine_restart.offset,
             C.sizeof(G.gpe_report), G.gpe_report.res_l2.offset, G.gpe_report.log.offset,
-            G.gpe_report.loop_kind.offset]
+            G.gpe_report.loop_kind.offset, G.gpe_report.iters_fp64.offset]
     assert got == want
 
 
@@ -101,6 +101,16 @@ def test_null_arguments(built_lib):
     assert lib.gpe_apply_H(None, None, None, None) == G.GPE_ERR_ARG
     assert lib.gpe_energy(None, None, None) == G.GPE_ERR_ARG
     assert lib.gpe_pcg_solve(None, None, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_set_problem(None, None, 1.0, 0.0) == G.GPE_ERR_ARG
+    assert lib.gpe_energy_grad(None, None, None, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_tangent_solve(None, None, None, None, 1e-10, 10, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_density_adjoint(None, None, None, None, 1e-10, 10, None, None) == G.GPE_ERR_ARG
+    out = C.c_void_p()
+    assert lib.gpe_batch_create(0, None, None, None, C.byref(out)) == G.GPE_ERR_ARG and not out.value
+    assert lib.gpe_batch_create(1, None, None, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_batch_solve(None, None, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_batch_destroy(None) == G.GPE_OK
+    assert lib.gpe_batch_last_error(None) is not None
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
