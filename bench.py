@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched sweep")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-kernel plans")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the same pass kernels from a host loop instead of one graph with a device-side "
                          "loop (for ncu launch lists: ncu cannot profile kernel nodes of graphs with conditional "
@@ -191,6 +193,12 @@ def main():
     n, L = w["n"], w["L"]
     N = int(np.prod(n))
     ctx = gpe.Context(n, L, w["eta"], w["omega"], w["V"], prec=gpe.GPE_MIXED)
+    # set-up, outside every timed region: the tuner picks the pass-kernel plans
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = ctx.autotune(iters=20)
+        tune["seconds"] = time.perf_counter() - t0
     phi0_d = torch.from_numpy(w["phi0"].copy()).to(dev)
     phi_d = torch.empty_like(phi0_d)
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -296,6 +304,7 @@ def main():
     if not args.no_secondary:
         w3 = I.workload("rot128_3d")
         ctx3 = gpe.Context(w3["n"], w3["L"], w3["eta"], w3["omega"], w3["V"], prec=gpe.GPE_MIXED)
+        plans3 = None if args.no_autotune else ctx3.autotune(iters=10)["plans"]
         p30 = torch.from_numpy(w3["phi0"].copy()).to(dev)
         p3 = torch.empty_like(p30)
         p3.copy_(p30)
@@ -312,8 +321,42 @@ def main():
             s3.append(a.elapsed_time(b))
         secondary = {"workload": "rot128_3d", "value": 1000.0 / statistics.mean(s3), "unit": UNIT,
                      "ms_per_step": statistics.mean(s3), "iters": r3["iters"], "iters_lo": r3["iters_lo"],
-                     "E": r3["E"], "res_inf": r3["res_inf"]}
+                     "E": r3["E"], "res_inf": r3["res_inf"], "plans": plans3}
         ctx3.close()
+
+    # ---------------- secondary: the 96-instance batched parameter sweep ----------------
+    batch = None
+    if not args.no_batch and rank == 0:
+        insts = I.sweep_instances(96)
+        arrays = [I.sweep_arrays(x) for x in insts]
+        specs = [dict(n=x["n"], L=x["L"], eta=x["eta"], omega=x["omega"], V=V, prec=gpe.GPE_MIXED)
+                 for x, (V, _) in zip(insts, arrays)]
+        bphi0 = [torch.from_numpy(p.copy()).to(dev) for _, p in arrays]
+        bphi = [torch.empty_like(p) for p in bphi0]
+        with gpe.Batch(specs) as B:
+            if not args.no_autotune:
+                B.autotune(iters=10)
+            bts = []
+            for k in range(2):  # the first launch builds the graph
+                for p, q in zip(bphi, bphi0):
+                    p.copy_(q)
+                l2_flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                bs, breps = B.solve(bphi)
+                b.record(stream)
+                b.synchronize()
+                if k:
+                    bts.append(a.elapsed_time(b))
+        bms = statistics.mean(bts)
+        batch = {"workload": "sweep96_2d (32 each of 128^2, 256^2, 512^2 on [-16,16]^2; omega U[0,0.95], "
+                             "eta {100,250,500,1000}, kappa {0,0.05})",
+                 "value": 96 * 1000.0 / bms, "unit": UNIT, "ms_per_step": bms,
+                 "launch": "one CUDA graph (gpe_batch_solve)",
+                 "converged": int(sum(r["status"] == gpe.GPE_OK for r in breps)),
+                 "iters_total": int(sum(r["iters"] for r in breps)),
+                 "fp64_completions": int(sum(r["iters_fp64"] > 0 for r in breps))}
+        del bphi, bphi0
 
     # ---------------- CPU baseline (oracle, bounded sample) ----------------
     cpu = None
@@ -337,7 +380,8 @@ def main():
                                 1: "graph", 0: "host loop"}[last["loop_kind"]],
                        "loop_note": last.get("note", ""),
                        "E": last["E"], "res_inf": last["res_inf"],
-                       "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}"},
+                       "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas{world}",
+                       "plans": tune and tune["plans"], "autotune_s": tune and tune["seconds"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": HPHI_TRAFFIC_PER_LAUNCH,
                          "kernel": "cluster_apply_H<float,256> (gpe_apply_H_batch: one 16-CTA cluster per field)",
@@ -348,6 +392,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "secondary": secondary,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -291,6 +291,42 @@ gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* op
 gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V_dev, const void* phi_dev, const void* f_dev,
                                void* out_dev, void* stream, char* err, size_t err_len);
 
+/* ---- Plans of the pass kernels and the tuner ------------------------------
+ * Every grid pass transforms lines of M points held by M/E threads with E
+ * values each (E = 8 or 4: the radix structure of the Stockham line transform,
+ * radix 8 then 8/4/2 stages for E = 8, radix-4 stages for E = 4), blocks of
+ * `width` lines (x passes) or tiles of `width` adjacent x-columns (y, z
+ * passes).  A plan (E, width) is kept per launch mode (0: complex64 passes,
+ * 1: FP64 passes, 2: refinement passes) and axis; the defaults are E = 8 and
+ * widths from a block-count heuristic.  Plans change the order of floating-
+ * point sums, not the method.  The paper has no counterpart (it runs serial
+ * full-grid FFTs). */
+typedef struct {
+  int cached;           /* 1: every plan came from an earlier tuning of the same grid in this process */
+  int candidates;       /* plans timed */
+  double us_before[3];  /* per mode: microseconds per iteration with the plans in use before the call
+                         * (0: mode not used by the context, or cached) */
+  double us_after[3];   /* with the chosen plans */
+  int E[3][3];          /* chosen [mode][axis] */
+  int width[3][3];
+} gpe_tune_report;
+
+/* Time candidate plans on this context's grid and keep the fastest per mode
+ * and axis: `iters` solver iterations (host-launched passes, from a
+ * normalised Gaussian) per candidate, coordinate descent over the axes, a new
+ * choice must be 2% faster.  use_cache != 0 reuses the plans tuned earlier in
+ * this process for the same grid and mode.  Overwrites the context's solver
+ * work buffers; discards its captured graphs.  Synchronises the stream.
+ * report may be NULL.  Errors: GPE_ERR_ARG, GPE_ERR_CUDA. */
+gpe_status gpe_autotune(gpe_ctx* ctx, int iters, int use_cache, gpe_tune_report* report);
+
+/* Set / read the plan of (mode, axis).  gpe_set_plan rejects plans the kernels
+ * cannot run (E not 4 or 8, E = 4 below M = 32, width not a power of two, more
+ * threads than the mode's kernels allow, too much shared memory, more blocks
+ * than the context's reduction buffers) with GPE_ERR_ARG. */
+gpe_status gpe_set_plan(gpe_ctx* ctx, int mode, int axis, int E, int width);
+gpe_status gpe_get_plan(const gpe_ctx* ctx, int mode, int axis, int* E, int* width);
+
 /* ---- Batched solves ------------------------------------------------------
  * Many independent ground states (different grids, eta, omega, V; Section 2
  * problems, each solved by the gpe_pcg_solve algorithm) in ONE graph launch.
@@ -319,6 +355,10 @@ gpe_status gpe_batch_create(int count, const gpe_problem* probs, const double* c
 gpe_status gpe_batch_solve(gpe_batch* batch, void* const* phi_inout, const gpe_solve_opts* opts, gpe_report* reports);
 
 gpe_status gpe_batch_destroy(gpe_batch* batch);
+
+/* gpe_autotune (with the process cache) on every instance's context; the
+ * batch graph is rebuilt with the chosen plans by the next gpe_batch_solve. */
+gpe_status gpe_batch_autotune(gpe_batch* batch, int iters);
 
 /* Last failure on batch ("" if none); NULL: the last failed gpe_batch_create. */
 const char* gpe_batch_last_error(const gpe_batch* batch);

@@ -9,6 +9,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <array>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/gpe.h"
@@ -22,9 +25,11 @@ using namespace gpe;
 namespace {
 
 constexpr int kTargetBlocks = 2 * 152;  // aim for >= 2 blocks per SM per pass
+constexpr int kPlanMaxBlocks = 4096;    // reduction partials reserved for tuned plans
 
 struct PassPlan {
   int lpb = 1, tx = 1, nblocks = 1, M = 8;
+  int E = 8;  // values per thread of the line transforms
   long long stride = 0, outer_stride = 0;
   int ntx = 1;
 };
@@ -62,7 +67,9 @@ struct gpe_ctx {
   unsigned* ticket = nullptr;
   double* log_dev = nullptr;
   int log_dev_cap = 0;
-  PassPlan plan[3];  // per axis
+  PassPlan plan[3];      // default plan per axis (E = 8, heuristic widths)
+  PassPlan mplan[3][3];  // plan used per launch mode [mode][axis] (the default, or the tuner's choice)
+  int partials_cap = 0;  // blocks the reduction partials buffer holds
   double vmax = 0.0;  // max V on the grid
   int max_threads[2] = {512, 256};
   bool warmed[3] = {false, false, false};  // per launch mode
@@ -100,7 +107,7 @@ static bool is_device_ptr(const void* p) {
 
 static void plan_axis(gpe_ctx* c, int axis, int maxT, PassPlan& pl) {
   const int M = c->n[axis];
-  const int Tl = M / 8;
+  const int Tl = M / pl.E;
   pl.M = M;
   if (axis == 0) {
     const long long nlines = (long long)c->n[1] * (c->dim == 3 ? c->n[2] : 1);
@@ -124,13 +131,15 @@ static void plan_axis(gpe_ctx* c, int axis, int maxT, PassPlan& pl) {
   }
 }
 
-static PassArgs base_args(gpe_ctx* c, int prec, int axis) {
+// Pass arguments for `axis` with the tables of precision `prec` and the plan
+// of launch mode `mode`.
+static PassArgs base_args(gpe_ctx* c, int prec, int axis, int mode) {
   PassArgs a;
   std::memset(&a, 0, sizeof(a));
-  const PassPlan& pl = c->plan[axis];
+  const PassPlan& pl = c->mplan[mode][axis];
   const PrecBufs& b = c->pb[prec];
   a.dim = c->dim; a.nx = c->n[0]; a.ny = c->n[1]; a.nz = c->dim == 3 ? c->n[2] : 1;
-  a.axis = axis; a.M = pl.M; a.lpb = pl.lpb; a.tx = pl.tx; a.stride = pl.stride;
+  a.axis = axis; a.M = pl.M; a.E = pl.E; a.lpb = pl.lpb; a.tx = pl.tx; a.stride = pl.stride;
   a.outer_stride = pl.outer_stride; a.ntx = pl.ntx; a.nblocks = pl.nblocks;
   a.weight = c->weight; a.eta = c->prob.eta; a.omega = c->prob.omega;
   for (int i = 0; i < 3; ++i) { a.xi[i] = b.xi[i]; a.xc[i] = b.xc[i]; }
@@ -321,9 +330,11 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
     // plan with the smaller (double) thread cap so one plan serves both precisions
     plan_axis(c, ax, c->max_threads[1], c->plan[ax]);
     if (c->plan[ax].nblocks > maxblocks) maxblocks = c->plan[ax].nblocks;
+    for (int m = 0; m < 3; ++m) c->mplan[m][ax] = c->plan[ax];
   }
+  c->partials_cap = maxblocks > kPlanMaxBlocks ? maxblocks : kPlanMaxBlocks;  // room for tuned plans
   if (cudaMalloc(&c->ctl_solve, sizeof(Ctl)) != cudaSuccess || cudaMalloc(&c->ctl_api, sizeof(Ctl)) != cudaSuccess ||
-      cudaMalloc(&c->partials, sizeof(double) * kMaxMoments * (size_t)maxblocks) != cudaSuccess ||
+      cudaMalloc(&c->partials, sizeof(double) * kMaxMoments * (size_t)c->partials_cap) != cudaSuccess ||
       cudaMalloc(&c->ticket, sizeof(unsigned)) != cudaSuccess) {
     c->err = "cudaMalloc workspace"; return fail(GPE_ERR_CUDA);
   }
@@ -357,11 +368,11 @@ extern "C" const char* gpe_last_error(const gpe_ctx* c) { return c ? c->err.c_st
 // H passes on (phi, f): t = A_x f + (V + eta|phi|^2) f, then the y (and z) parts
 // accumulated; the last one writes `out` (or t) and finalises the energy terms.
 static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, void* out, Ctl* ctl) {
-  PassArgs a = base_args(c, prec, 0);
+  PassArgs a = base_args(c, prec, 0, prec);
   a.ctl = ctl; a.phi = phi; a.f = f; a.t = c->pb[prec].t;
   GPE_CU(c, launch(prec, P_HX, a, c->st));
   for (int ax = 1; ax < c->dim; ++ax) {
-    PassArgs b = base_args(c, prec, ax);
+    PassArgs b = base_args(c, prec, ax, prec);
     b.ctl = ctl; b.phi = phi; b.f = f; b.t = c->pb[prec].t;
     b.last_axis = (ax == c->dim - 1);
     b.out = b.last_axis ? out : nullptr;
@@ -462,21 +473,21 @@ static gpe_status tangent_solve(gpe_ctx* c, const void* phi, const void* rhs, vo
 // P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
 static gpe_status run_PC(gpe_ctx* c, const IterBufs& b, const void* r, double alpha, void* out, Ctl* ctl,
                          bool solver, cudaStream_t st) {
-  PassArgs a = base_args(c, b.tab_d, 0);
+  PassArgs a = base_args(c, b.tab_d, 0, b.mode);
   a.V = b.V;
   a.ctl = ctl; a.solver = solver; a.phi = b.phi; a.r_in = r; a.api_alpha = alpha;
   a.s = b.s; a.t = b.t; a.r_prev = b.r_prev; a.p = b.p; a.out = out;
   GPE_CU(c, launch(b.mode, P_C1, a, st));
   if (c->dim == 3) {
-    PassArgs y = base_args(c, b.tab_d, 1);
+    PassArgs y = base_args(c, b.tab_d, 1, b.mode);
     y.ctl = ctl; y.solver = solver; y.s = b.s;
     GPE_CU(c, launch(b.mode, P_CFWD, y, st));
   }
-  PassArgs k = base_args(c, b.tab_d, c->dim - 1);
+  PassArgs k = base_args(c, b.tab_d, c->dim - 1, b.mode);
   k.ctl = ctl; k.solver = solver; k.s = b.s; k.api_alpha = alpha;
   GPE_CU(c, launch(b.mode, P_CCORE, k, st));
   if (c->dim == 3) {
-    PassArgs y = base_args(c, b.tab_d, 1);
+    PassArgs y = base_args(c, b.tab_d, 1, b.mode);
     y.ctl = ctl; y.solver = solver; y.s = b.s;
     GPE_CU(c, launch(b.mode, P_CINV, y, st));
   }
@@ -616,32 +627,32 @@ static IterArgs iter_args(gpe_ctx* c, int mode, unsigned long long cond) {
   Ctl* ctl = c->ctl_solve;
   IterArgs I;
   // H phi (with the retraction phi_{n+1} = (c phi_n + s p_n/|p_n|)/nrm folded into the x pass)
-  I.hx = base_args(c, b.tab_h, 0);
+  I.hx = base_args(c, b.tab_h, 0, mode);
   I.hx.V = b.V;
   I.hx.ctl = ctl; I.hx.solver = 1; I.hx.phi = b.phi; I.hx.phi_out = b.phi; I.hx.p = b.p; I.hx.t = b.t;
   for (int ax = 1; ax < 3; ++ax) {
     PassArgs& h = I.hmid[ax - 1];
-    h = base_args(c, b.tab_h, ax < c->dim ? ax : 0);
+    h = base_args(c, b.tab_h, ax < c->dim ? ax : 0, mode);
     h.ctl = ctl; h.solver = 1; h.phi = b.phi; h.t = b.t; h.last_axis = (ax == c->dim - 1);
   }
   // P_C r_n
-  I.c1 = base_args(c, b.tab_d, 0);
+  I.c1 = base_args(c, b.tab_d, 0, mode);
   I.c1.V = b.V;
   I.c1.ctl = ctl; I.c1.solver = 1; I.c1.phi = b.phi; I.c1.s = b.s; I.c1.t = b.t; I.c1.r_prev = b.r_prev; I.c1.p = b.p;
   I.c3 = I.c1;
   const int ay = c->dim == 3 ? 1 : 0;
-  I.cfwd = base_args(c, b.tab_d, ay);
+  I.cfwd = base_args(c, b.tab_d, ay, mode);
   I.cfwd.ctl = ctl; I.cfwd.solver = 1; I.cfwd.s = b.s;
   I.cinv = I.cfwd;
-  I.ccore = base_args(c, b.tab_d, c->dim - 1);
+  I.ccore = base_args(c, b.tab_d, c->dim - 1, mode);
   I.ccore.ctl = ctl; I.ccore.solver = 1; I.ccore.s = b.s;
   // p_n and the step-size moments
-  I.ax = base_args(c, b.tab_d, 0);
+  I.ax = base_args(c, b.tab_d, 0, mode);
   I.ax.V = b.V;
   I.ax.ctl = ctl; I.ax.solver = 1; I.ax.phi = b.phi; I.ax.s = b.s; I.ax.t = b.t; I.ax.p = b.p;
   for (int ax = 1; ax < 3; ++ax) {
     PassArgs& m = I.amid[ax - 1];
-    m = base_args(c, b.tab_d, ax < c->dim ? ax : 0);
+    m = base_args(c, b.tab_d, ax < c->dim ? ax : 0, mode);
     m.ctl = ctl; m.solver = 1; m.phi = b.phi; m.p = b.p; m.last_axis = (ax == c->dim - 1);
     m.cond = m.last_axis ? cond : 0ull;
   }
@@ -866,6 +877,205 @@ static gpe_status check_opts(gpe_solve_opts& o, std::string& err) {
     return GPE_ERR_ARG;
   }
   if (o.max_iter_lo <= 0) o.max_iter_lo = o.max_iter;
+  return GPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plans of the pass kernels and their tuner
+// ---------------------------------------------------------------------------
+// Thread cap of a launch mode's kernels (launch bounds: 512 with single-
+// precision transforms, 256 once a double or double-single type is involved)
+// and the largest element size its passes stage in shared memory.
+static int mode_max_threads(int mode) { return mode == 0 ? 512 : 256; }
+static size_t mode_elem_bytes(int mode) { return mode == 0 ? 8 : 16; }
+static bool mode_available(const gpe_ctx* c, int mode) { return mode >= 0 && mode < 3 && c->pb[mode].on; }
+
+// A plan for (mode, axis): E values per thread (4 or 8), `width` lines per
+// block (axis 0) or adjacent x-columns per tile (axes 1, 2).  False when the
+// kernels cannot run it (thread cap, shared memory, partials capacity).
+static bool make_plan(const gpe_ctx* c, int mode, int axis, int E, int width, PassPlan& pl) {
+  if (axis < 0 || axis >= c->dim) return false;
+  const int M = c->n[axis];
+  if (!(E == 8 || (E == 4 && M >= 32))) return false;
+  if (width < 1 || (width & (width - 1)) != 0) return false;
+  const int Tl = M / E;
+  if ((long long)Tl * width > mode_max_threads(mode)) return false;
+  PassPlan q;
+  q.M = M;
+  q.E = E;
+  if (axis == 0) {
+    const long long nlines = (long long)c->n[1] * (c->dim == 3 ? c->n[2] : 1);
+    if (width > nlines) return false;
+    if ((size_t)width * (M + M / 16) * mode_elem_bytes(mode) > 200 * 1024) return false;
+    q.lpb = width;
+    q.nblocks = (int)(nlines / width);
+  } else {
+    const int nx = c->n[0];
+    if (width > nx) return false;
+    if ((size_t)M * width * mode_elem_bytes(mode) > 200 * 1024) return false;
+    const long long outer = (axis == 1) ? (c->dim == 3 ? c->n[2] : 1) : c->n[1];
+    q.tx = width;
+    q.ntx = nx / width;
+    q.nblocks = (int)((long long)q.ntx * outer);
+    q.stride = (axis == 1) ? nx : (long long)nx * c->n[1];
+    q.outer_stride = (axis == 1) ? (long long)nx * c->n[1] : nx;
+  }
+  if (q.nblocks < 1 || q.nblocks > c->partials_cap) return false;
+  pl = q;
+  return true;
+}
+
+static void plans_changed(gpe_ctx* c, int mode) {
+  if (c->exec[mode]) cudaGraphExecDestroy(c->exec[mode]);
+  c->exec[mode] = nullptr;
+  c->warmed[mode] = false;
+}
+
+extern "C" gpe_status gpe_set_plan(gpe_ctx* c, int mode, int axis, int E, int width) {
+  if (!c) return GPE_ERR_ARG;
+  if (!mode_available(c, mode)) { c->err = "launch mode not used by this context"; return GPE_ERR_ARG; }
+  PassPlan pl;
+  if (!make_plan(c, mode, axis, E, width, pl)) { c->err = "plan not supported for this grid and mode"; return GPE_ERR_ARG; }
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  c->mplan[mode][axis] = pl;
+  plans_changed(c, mode);
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_get_plan(const gpe_ctx* c, int mode, int axis, int* E, int* width) {
+  if (!c || !E || !width || mode < 0 || mode > 2 || axis < 0 || axis >= c->dim) return GPE_ERR_ARG;
+  const PassPlan& pl = c->mplan[mode][axis];
+  *E = pl.E;
+  *width = axis == 0 ? pl.lpb : pl.tx;
+  return GPE_OK;
+}
+
+// Microseconds per iteration of launch mode `mode` with the current plans:
+// `iters` solver iterations (host-launched passes, after two warm-up
+// iterations) from a normalised Gaussian, best of two runs.
+static gpe_status tune_time(gpe_ctx* c, int mode, int iters, const std::vector<double>& g128, double* us) {
+  const IterBufs b = iter_bufs(c, mode);
+  cudaStream_t st = c->st;
+  const long long N = c->N;
+  gpe_solve_opts o;
+  gpe_solve_opts_default(&o);
+  o.tol_res_inf = 0.0;
+  o.max_iter = 1 << 30;
+  Ctl h = solve_ctl(c, o, 0);
+  h.lo_phase = 0; h.phase = 1; h.max_iter_phase = o.max_iter; h.stall_switch = 0;
+  cudaEvent_t e0, e1;
+  GPE_CU(c, cudaEventCreate(&e0));
+  GPE_CU(c, cudaEventCreate(&e1));
+  double best = 1e300;
+  gpe_status s = GPE_OK;
+  for (int rep = 0; rep < 2 && s == GPE_OK; ++rep) {
+    cudaError_t e = cudaMemcpyAsync(c->pb[1].phi, g128.data(), 16 * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && mode != 1) e = launch_convert_c128_to_c64(c->pb[1].phi, c->pb[0].phi, N, st);
+    if (e == cudaSuccess && mode == 2) e = launch_convert_c64_to_ds(c->pb[0].phi, c->pb[2].phi, N, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.p, 0, (b.tab_d ? 16 : 8) * (size_t)N, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.r_prev, 0, (b.tab_h ? 16 : 8) * (size_t)N, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_init_norm(b.tab_h, b.phi, N, c->weight, c->ctl_solve, st);
+    if (e != cudaSuccess) { c->err = std::string("tuner set-up: ") + cudaGetErrorString(e); s = GPE_ERR_CUDA; break; }
+    for (int k = 0; k < 2 && s == GPE_OK; ++k) s = enqueue_iteration(c, mode, st, 0ull);
+    if (s != GPE_OK) break;
+    e = cudaEventRecord(e0, st);
+    for (int k = 0; k < iters && s == GPE_OK && e == cudaSuccess; ++k) s = enqueue_iteration(c, mode, st, 0ull);
+    if (s != GPE_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { c->err = std::string("tuner timing: ") + cudaGetErrorString(e); s = GPE_ERR_CUDA; break; }
+    const double t = 1000.0 * ms / iters;
+    best = t < best ? t : best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *us = best;
+  return s;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, std::array<PassPlan, 3>> g_tune_cache;  // (dim, n, mode) -> plans per axis
+}  // namespace
+
+extern "C" gpe_status gpe_autotune(gpe_ctx* c, int iters, int use_cache, gpe_tune_report* rep) {
+  if (!c) return GPE_ERR_ARG;
+  if (iters < 1) { c->err = "iters must be >= 1"; return GPE_ERR_ARG; }
+  gpe_tune_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.cached = 1;
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  // a normalised Gaussian exp(-|x|^2 / 2) on the grid (host, FP64)
+  std::vector<double> g128(2 * (size_t)c->N, 0.0);
+  {
+    double nrm = 0.0;
+    for (long long i = 0; i < c->N; ++i) {
+      long long k = i;
+      double r2 = 0.0;
+      for (int ax = 0; ax < c->dim; ++ax) {
+        const double x = -c->prob.L[ax] + (double)(k % c->n[ax]) * c->h[ax];
+        k /= c->n[ax];
+        r2 += x * x;
+      }
+      g128[2 * i] = std::exp(-0.5 * r2);
+      nrm += g128[2 * i] * g128[2 * i];
+    }
+    const double sc = 1.0 / std::sqrt(nrm * c->weight);
+    for (long long i = 0; i < c->N; ++i) g128[2 * i] *= sc;
+  }
+  for (int mode = 0; mode < 3; ++mode) {
+    if (!mode_available(c, mode)) continue;
+    const std::array<int, 5> key = {c->dim, c->n[0], c->n[1], c->dim == 3 ? c->n[2] : 1, mode};
+    bool hit = false;
+    if (use_cache) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        for (int ax = 0; ax < c->dim; ++ax) c->mplan[mode][ax] = it->second[ax];
+        hit = true;
+      }
+    }
+    if (!hit) {
+      r.cached = 0;
+      double cur = 0.0;
+      gpe_status s = tune_time(c, mode, iters, g128, &cur);
+      if (s != GPE_OK) return s;
+      r.us_before[mode] = cur;
+      // coordinate descent over the axes: every (E, width) for one axis with
+      // the other axes at their current choice; a change must gain 2%
+      for (int ax = 0; ax < c->dim; ++ax) {
+        PassPlan best = c->mplan[mode][ax];
+        for (int E : {8, 4}) {
+          for (int w = 1; w <= 512; w *= 2) {
+            PassPlan cand;
+            if (!make_plan(c, mode, ax, E, w, cand)) continue;
+            if (cand.E == best.E && cand.lpb == best.lpb && cand.tx == best.tx) continue;
+            c->mplan[mode][ax] = cand;
+            double t = 0.0;
+            s = tune_time(c, mode, iters, g128, &t);
+            ++r.candidates;
+            if (s != GPE_OK) { c->mplan[mode][ax] = best; return s; }
+            if (t < 0.98 * cur) { cur = t; best = cand; }
+          }
+        }
+        c->mplan[mode][ax] = best;
+      }
+      r.us_after[mode] = cur;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      std::array<PassPlan, 3> pl;
+      for (int ax = 0; ax < 3; ++ax) pl[ax] = c->mplan[mode][ax];
+      g_tune_cache[key] = pl;
+    }
+    for (int ax = 0; ax < c->dim; ++ax) {
+      r.E[mode][ax] = c->mplan[mode][ax].E;
+      r.width[mode][ax] = ax == 0 ? c->mplan[mode][ax].lpb : c->mplan[mode][ax].tx;
+    }
+    plans_changed(c, mode);
+  }
+  if (rep) *rep = r;
   return GPE_OK;
 }
 
@@ -1195,6 +1405,17 @@ extern "C" gpe_status gpe_batch_solve(gpe_batch* B, void* const* phi_inout, cons
     return (gpe_status)first_bad;
   }
   B->err.clear();
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_batch_autotune(gpe_batch* B, int iters) {
+  if (!B) return GPE_ERR_ARG;
+  for (gpe_ctx* c : B->ctx) {
+    const gpe_status s = gpe_autotune(c, iters, 1, nullptr);
+    if (s != GPE_OK) { B->err = c->err; return s; }
+  }
+  if (B->exec) cudaGraphExecDestroy(B->exec);  // rebuilt with the new plans by the next solve
+  B->exec = nullptr;
   return GPE_OK;
 }
 

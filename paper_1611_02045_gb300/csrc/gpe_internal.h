@@ -76,6 +76,7 @@ struct PassArgs {
   int dim, nx, ny, nz;
   int axis;        // physical axis transformed by this pass
   int M;           // length along that axis
+  int E;           // values per thread of the line transforms: 4, or 8 (also when 0)
   int lpb;         // contiguous passes: lines per block
   int row0;        // contiguous passes: global row of line 0 (field slices held by one CTA)
   int tx;          // strided passes: tile width in x
@@ -122,6 +123,14 @@ cudaError_t launch_group_f64_h(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_c(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_f64_a(Pass pass, const PassArgs& a, cudaStream_t st);
 cudaError_t launch_group_split(Pass pass, const PassArgs& a, cudaStream_t st);
+// The same groups with E = 4 values per thread (PassArgs::E == 4; M >= 32).
+cudaError_t launch_group_f32_h_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f32_c_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f32_a_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_h_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_c_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_f64_a_e4(Pass pass, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_group_split_e4(Pass pass, const PassArgs& a, cudaStream_t st);
 
 // H phi on a batch of 2D fields, one thread-block cluster per field
 // (gpe_cluster.cu); args is a ClusterHArgs (gpe_cluster.cuh).

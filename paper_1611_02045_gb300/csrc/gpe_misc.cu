@@ -21,7 +21,31 @@ static cudaError_t launch_pass_f64(Pass pass, const PassArgs& a, cudaStream_t st
   }
 }
 
+static cudaError_t launch_pass_f32_e4(Pass pass, const PassArgs& a, cudaStream_t st) {
+  switch (pass) {
+    case P_HX: case P_HMID: return launch_group_f32_h_e4(pass, a, st);
+    case P_AX: case P_AMID: return launch_group_f32_a_e4(pass, a, st);
+    default: return launch_group_f32_c_e4(pass, a, st);
+  }
+}
+
+static cudaError_t launch_pass_e4(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
+  if (mode == 0) return launch_pass_f32_e4(pass, a, st);
+  if (mode == 1) {
+    switch (pass) {
+      case P_HX: case P_HMID: return launch_group_f64_h_e4(pass, a, st);
+      case P_AX: case P_AMID: return launch_group_f64_a_e4(pass, a, st);
+      default: return launch_group_f64_c_e4(pass, a, st);
+    }
+  }
+  switch (pass) {
+    case P_HX: case P_HMID: case P_C1: case P_C3: case P_AX: return launch_group_split_e4(pass, a, st);
+    default: return launch_pass_f32_e4(pass, a, st);
+  }
+}
+
 cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
+  if (a.E == 4) return launch_pass_e4(mode, pass, a, st);
   if (mode == 0) return launch_pass_f32(pass, a, st);
   if (mode == 1) return launch_pass_f64(pass, a, st);
   // refinement split: H phi and the state in double-single, the strided

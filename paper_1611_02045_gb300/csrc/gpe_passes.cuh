@@ -32,10 +32,13 @@ namespace gpe {
 
 enum StatusCode { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_NOT_CONVERGED = 3, ST_NONFINITE = 4, ST_PRECOND = 5 };
 
-template <int M> struct LineCfg {
-  static constexpr int E = 8;     // values per thread
+// A line of M points is held by Tl = M / E threads, E values each (E = 8 by
+// default; E = 4 doubles the threads per line for latency-bound passes).
+template <int M, int EV = 8> struct LineCfg {
+  static constexpr int E = EV;      // values per thread
   static constexpr int Tl = M / E;  // threads per line
   static_assert(M >= 8 && (M & (M - 1)) == 0, "M must be a power of two >= 8");
+  static_assert((EV == 4 || EV == 8) && M >= EV, "E must be 4 or 8");
 };
 
 // ---------------------------------------------------------------------------
@@ -393,13 +396,13 @@ __device__ __forceinline__ cplx<To> cconv(From v) { return cmk<cplx<To>>((To)v.x
 // One unit of a contiguous pass: lines unit*lpb .. unit*lpb + lpb - 1 (the
 // block has lpb * M/8 threads).  Adds this thread's reduction terms to acc[]
 // (Moments<ROLE>: sums, or maxima for the slots flagged in MAX).
-template <typename TF, typename TS, typename TD, int M, int ROLE>
+template <typename TF, typename TS, typename TD, int M, int ROLE, int EV = 8>
 __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long long unit, unsigned char* smraw,
                                       Acc* acc) {
   using CF = cplx<TF>;
   using CS = cplx<TS>;
   using CD = cplx<TD>;
-  constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
+  constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
   constexpr int LS = M + M / 16;  // padded line stride in shared memory
   CF* sm = reinterpret_cast<CF*>(smraw);
 
@@ -604,11 +607,11 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
 // ---------------------------------------------------------------------------
 // One unit of a strided pass: the tile of tx adjacent x-columns number unit
 // (block = tx * M/8 threads).  Reduction terms are added to acc[].
-template <typename T, int M, int ROLE>
+template <typename T, int M, int ROLE, int EV = 8>
 __device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long long unit, unsigned char* smraw,
                                       Acc* acc) {
   using C = cplx<T>;
-  constexpr int E = LineCfg<M>::E, Tl = LineCfg<M>::Tl;
+  constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
   C* sm = reinterpret_cast<C*>(smraw);
   const int tx = a.tx;
   const int c = threadIdx.x % tx, t = threadIdx.x / tx;
@@ -743,7 +746,7 @@ __device__ __forceinline__ void reduce_and_finish(const PassArgs& a, const Acc* 
   }
 }
 
-template <typename TF, typename TS, typename TD, int M, int ROLE>
+template <typename TF, typename TS, typename TD, int M, int ROLE, int EV>
 __global__ void __launch_bounds__(MaxThreads<TF>::value < MaxThreads<TS>::value ? MaxThreads<TF>::value : MaxThreads<TS>::value) pass_x(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.solver && a.ctl->done) return;
@@ -751,11 +754,11 @@ __global__ void __launch_bounds__(MaxThreads<TF>::value < MaxThreads<TS>::value 
   Acc acc[kMaxMoments];
 #pragma unroll
   for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
-  xunit<TF, TS, TD, M, ROLE>(a, S, blockIdx.x, smraw, acc);
+  xunit<TF, TS, TD, M, ROLE, EV>(a, S, blockIdx.x, smraw, acc);
   reduce_and_finish<ROLE>(a, acc);
 }
 
-template <typename T, int M, int ROLE>
+template <typename T, int M, int ROLE, int EV>
 __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (a.solver && a.ctl->done) {
@@ -766,7 +769,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) pass_s(PassArgs a) {
   Acc acc[kMaxMoments];
 #pragma unroll
   for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
-  sunit<T, M, ROLE>(a, S, blockIdx.x, smraw, acc);
+  sunit<T, M, ROLE, EV>(a, S, blockIdx.x, smraw, acc);
   reduce_and_finish<ROLE>(a, acc);
 }
 
@@ -787,12 +790,12 @@ template <int ROLE> struct ModeTypes<2, ROLE> {
   using TD = float;
 };
 
-template <int MODE, int M, int ROLE>
+template <int MODE, int M, int ROLE, int EV>
 cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
   using MT = ModeTypes<MODE, ROLE>;
   using TF = typename MT::TF;
   using C = cplx<TF>;
-  constexpr int Tl = LineCfg<M>::Tl;
+  constexpr int Tl = LineCfg<M, EV>::Tl;
   constexpr bool contig = (ROLE == P_HX || ROLE == P_C1 || ROLE == P_C3 || ROLE == P_AX);
   int threads, smem;
   if constexpr (contig) {
@@ -803,8 +806,8 @@ cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
     smem = M * a.tx * (int)sizeof(C);
   }
   void (*kern)(PassArgs);
-  if constexpr (contig) kern = pass_x<TF, typename MT::TS, typename MT::TD, M, ROLE>;
-  else kern = pass_s<TF, M, ROLE>;
+  if constexpr (contig) kern = pass_x<TF, typename MT::TS, typename MT::TD, M, ROLE, EV>;
+  else kern = pass_s<TF, M, ROLE, EV>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -815,17 +818,30 @@ cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int MODE, int ROLE>
+// E = 8 for every M; E = 4 (plans chosen by the tuner) for M >= 32, in
+// their own translation units (gpe_k_e4_*.cu).
+template <int MODE, int ROLE, int EV = 8>
 cudaError_t launch_role(const PassArgs& a, cudaStream_t st) {
-  switch (a.M) {
-    case 8: return launch_one<MODE, 8, ROLE>(a, st);
-    case 16: return launch_one<MODE, 16, ROLE>(a, st);
-    case 32: return launch_one<MODE, 32, ROLE>(a, st);
-    case 64: return launch_one<MODE, 64, ROLE>(a, st);
-    case 128: return launch_one<MODE, 128, ROLE>(a, st);
-    case 256: return launch_one<MODE, 256, ROLE>(a, st);
-    case 512: return launch_one<MODE, 512, ROLE>(a, st);
-    default: return cudaErrorInvalidValue;
+  if constexpr (EV == 8) {
+    switch (a.M) {
+      case 8: return launch_one<MODE, 8, ROLE, 8>(a, st);
+      case 16: return launch_one<MODE, 16, ROLE, 8>(a, st);
+      case 32: return launch_one<MODE, 32, ROLE, 8>(a, st);
+      case 64: return launch_one<MODE, 64, ROLE, 8>(a, st);
+      case 128: return launch_one<MODE, 128, ROLE, 8>(a, st);
+      case 256: return launch_one<MODE, 256, ROLE, 8>(a, st);
+      case 512: return launch_one<MODE, 512, ROLE, 8>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (a.M) {
+      case 32: return launch_one<MODE, 32, ROLE, EV>(a, st);
+      case 64: return launch_one<MODE, 64, ROLE, EV>(a, st);
+      case 128: return launch_one<MODE, 128, ROLE, EV>(a, st);
+      case 256: return launch_one<MODE, 256, ROLE, EV>(a, st);
+      case 512: return launch_one<MODE, 512, ROLE, EV>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 

@@ -45,6 +45,11 @@ class gpe_report(C.Structure):
                 ("log", C.POINTER(C.c_double)), ("loop_kind", C.c_int), ("iters_fp64", C.c_int)]
 
 
+class gpe_tune_report(C.Structure):
+    _fields_ = [("cached", C.c_int), ("candidates", C.c_int), ("us_before", C.c_double * 3),
+                ("us_after", C.c_double * 3), ("E", (C.c_int * 3) * 3), ("width", (C.c_int * 3) * 3)]
+
+
 class GpeError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libgpe status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
@@ -55,7 +60,8 @@ _lib = None
 EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_apply_H_batch", "gpe_precond",
             "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
             "gpe_pcg_solve", "gpe_last_error", "gpe_batch_create", "gpe_batch_solve", "gpe_batch_destroy",
-            "gpe_batch_last_error")
+            "gpe_batch_last_error", "gpe_autotune", "gpe_set_plan", "gpe_get_plan", "gpe_batch_autotune")
+MODE_NAMES = ("complex64", "fp64", "refinement")
 _STRING_RETURNING = ("gpe_last_error", "gpe_batch_last_error")
 
 
@@ -88,6 +94,10 @@ def lib():
         L.gpe_batch_destroy.argtypes = [vp]
         L.gpe_batch_last_error.argtypes = [vp]
         L.gpe_batch_last_error.restype = C.c_char_p
+        L.gpe_autotune.argtypes = [vp, C.c_int, C.c_int, C.POINTER(gpe_tune_report)]
+        L.gpe_set_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.gpe_get_plan.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.gpe_batch_autotune.argtypes = [vp, C.c_int]
         for name in EXPORTED:
             if name not in _STRING_RETURNING:
                 getattr(L, name).restype = C.c_int
@@ -178,6 +188,24 @@ class Context:
         self._check(lib().gpe_energy_grad(self._ctx, _addr(phi), _addr(grad_phi), _addr(grad_V), out))
         keys = ("E", "dE_deta", "dE_domega", "lam", "norm2")
         return dict(zip(keys, list(out)))
+
+    def autotune(self, iters=20, use_cache=True):
+        """gpe_autotune: returns dict(cached, candidates, us_before, us_after, plans) with
+        plans[mode_name] = [(E, width) per axis] for the modes the context uses."""
+        r = gpe_tune_report()
+        self._check(lib().gpe_autotune(self._ctx, int(iters), int(bool(use_cache)), C.byref(r)))
+        plans = {MODE_NAMES[m]: [(r.E[m][a], r.width[m][a]) for a in range(self.dim)]
+                 for m in range(3) if r.E[m][0]}
+        return dict(cached=bool(r.cached), candidates=r.candidates, us_before=list(r.us_before),
+                    us_after=list(r.us_after), plans=plans)
+
+    def set_plan(self, mode, axis, E, width):
+        return self._check(lib().gpe_set_plan(self._ctx, int(mode), int(axis), int(E), int(width)))
+
+    def get_plan(self, mode, axis):
+        E, w = C.c_int(0), C.c_int(0)
+        self._check(lib().gpe_get_plan(self._ctx, int(mode), int(axis), C.byref(E), C.byref(w)))
+        return E.value, w.value
 
     def tangent_solve(self, phi, rhs, z, tol=1e-10, max_iter=2000, check=True):
         """gpe_tangent_solve: z with <phi, z> = 0 solving P K z = P rhs.  Returns
@@ -292,6 +320,11 @@ class Batch:
                     fallbacks=r.fallbacks, backtracks=r.backtracks, E=r.E, lam=r.lambda_, res_inf=r.res_inf,
                     res_l2=r.res_l2, loop_kind=r.loop_kind, iters_fp64=r.iters_fp64) for r in reps]
         return s, out
+
+    def autotune(self, iters=20):
+        s = lib().gpe_batch_autotune(self._b, int(iters))
+        if s != GPE_OK:
+            raise GpeError(s, lib().gpe_batch_last_error(self._b).decode())
 
     def close(self):
         if getattr(self, "_b", None):

@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--single", choices=["none", "fp64", "mixed"], default="none",
                     help="also time every instance solved alone, in this precision")
     ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-kernel plans")
     a = ap.parse_args()
 
     import torch
@@ -41,8 +42,10 @@ def main():
     opts = gpe.solve_opts_default()
     opts.max_iter = a.max_iter
 
-    out = dict(bench="sweep", count=a.count, grids=sorted({w["n"][0] for w in insts}))
+    out = dict(bench="sweep", count=a.count, grids=sorted({w["n"][0] for w in insts}), autotune=not a.no_autotune)
     with gpe.Batch(specs) as B:
+        if not a.no_autotune:
+            B.autotune(iters=10)  # one tuning per distinct grid (process cache)
         phis = [torch.empty_like(p) for p in phi0]
         times, reps = [], None
         for k in range(a.warmup + a.steps):
@@ -69,6 +72,8 @@ def main():
         tot, ok1, its = 0.0, 0, 0
         for w, (V, _), p0 in zip(insts, arrays, phi0):
             with gpe.Context(w["n"], w["L"], w["eta"], w["omega"], V, prec=prec) as ctx:
+                if not a.no_autotune:
+                    ctx.autotune(iters=10)
                 phi = p0.clone()
                 ctx.pcg_solve(phi.clone(), opts)  # builds the graphs
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -47,6 +47,8 @@ int main(void) {
          offsetof(gpe_solve_opts, refine_restart));
   printf("%zu %zu %zu %zu %zu\n", sizeof(gpe_report), offsetof(gpe_report, res_l2), offsetof(gpe_report, log),
          offsetof(gpe_report, loop_kind), offsetof(gpe_report, iters_fp64));
+  printf("%zu %zu %zu %zu\n", sizeof(gpe_tune_report), offsetof(gpe_tune_report, us_before),
+         offsetof(gpe_tune_report, E), offsetof(gpe_tune_report, width));
   return 0;
 }
 """
@@ -61,7 +63,9 @@ int main(void) {
             C.sizeof(G.gpe_solve_opts), G.gpe_solve_opts.switch_res.offset, G.gpe_solve_opts.use_graph.offset,
             G.gpe_solve_opts.refine_restart.offset,
             C.sizeof(G.gpe_report), G.gpe_report.res_l2.offset, G.gpe_report.log.offset,
-            G.gpe_report.loop_kind.offset, G.gpe_report.iters_fp64.offset]
+            G.gpe_report.loop_kind.offset, G.gpe_report.iters_fp64.offset,
+            C.sizeof(G.gpe_tune_report), G.gpe_tune_report.us_before.offset, G.gpe_tune_report.E.offset,
+            G.gpe_tune_report.width.offset]
     assert got == want
 
 
@@ -111,6 +115,10 @@ def test_null_arguments(built_lib):
     assert lib.gpe_batch_solve(None, None, None, None) == G.GPE_ERR_ARG
     assert lib.gpe_batch_destroy(None) == G.GPE_OK
     assert lib.gpe_batch_last_error(None) is not None
+    assert lib.gpe_autotune(None, 10, 1, None) == G.GPE_ERR_ARG
+    assert lib.gpe_set_plan(None, 0, 0, 8, 1) == G.GPE_ERR_ARG
+    assert lib.gpe_get_plan(None, 0, 0, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_batch_autotune(None, 10) == G.GPE_ERR_ARG
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -1,0 +1,182 @@
+"""Plans of the pass kernels (values per thread E, block / tile width) and the
+tuner (gpe_set_plan, gpe_autotune) on the GPU, against the FP64 CPU oracle.
+
+A plan only changes how lines are split over threads and blocks (and so the
+order of floating-point sums), so every plan must meet the same tolerances as
+the default one: operators rel 1e-12 (complex128) / 2e-5 (complex64), FP64
+per-iterate E_n rel 1e-12 and phase-aligned phi_n L2 1e-9 over 20 iterations,
+mixed solves E rel 1e-7 of the oracle's FP64 answer with ||r||_inf < 1e-8.
+"""
+import numpy as np
+import pytest
+
+from oracle import gpe_oracle as O
+from paper_1611_02045_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODE_C64, MODE_FP64, MODE_REFINE = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def G(built_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_02045_gb300 import gpe
+    return gpe
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def phase_aligned_rel_l2(a, b):
+    z = np.vdot(a, b)
+    return float(np.linalg.norm(a * (z / abs(z)) - b) / np.linalg.norm(b))
+
+
+def widths(n, axis, E, max_threads):
+    """Every power-of-two width the kernels accept for this axis (as gpe_set_plan)."""
+    M = n[axis]
+    Tl = M // E
+    out, w = [], 1
+    lines = int(np.prod(n[1:]))
+    while Tl * w <= max_threads and w <= (lines if axis == 0 else n[0]):
+        out.append(w)
+        w *= 2
+    return out
+
+
+PLAN_GRIDS = [((64, 64), (8.0, 8.0)), ((32, 128), (4.0, 10.0)), ((256, 256), (16.0, 16.0)),
+              ((32, 64, 32), (5.0, 6.0, 5.0)), ((512, 512), (16.0, 16.0))]
+
+
+@pytest.mark.parametrize("n,L", PLAN_GRIDS)
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_operators_match_oracle_under_every_E(G, n, L, prec):
+    """apply_H and P_C with E = 4 and E = 8 on every axis, at the smallest,
+    a middle and the largest width each axis accepts."""
+    V = I.harmonic(n, L, [1.0, 1.0, 2.0][: len(n)])
+    eta, om = 37.0, 0.7
+    po = O.Problem(n, L, eta, om, V)
+    mode, cap = (MODE_FP64, 256) if prec == 0 else (MODE_C64, 512)
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    tol = 1e-12 if prec == 0 else 2e-5
+    phi, f = I.random_field(1, n, L), I.random_field(2, n, L)
+    ph_d, f_d = dev(phi, dt), dev(f, dt)
+    out = torch.empty_like(f_d)
+    want_H = O.apply_H(po, host(ph_d), host(f_d))
+    want_P = O.precond_C(po, host(ph_d), host(f_d), 1.3)
+    with G.Context(n, L, eta, om, V, prec=prec) as ctx:
+        for E in (8, 4):
+            ws = [widths(n, ax, E, cap) for ax in range(len(n))]
+            for pick in (0, len(ws[0]) // 2, -1):
+                for ax in range(len(n)):
+                    ctx.set_plan(mode, ax, E, ws[ax][min(pick, len(ws[ax]) - 1) if pick >= 0 else -1])
+                    assert ctx.get_plan(mode, ax)[0] == E
+                ctx.apply_H(ph_d, f_d, out)
+                assert relmax(host(out), want_H) < tol, (E, pick)
+                ctx.precond(ph_d, f_d, 1.3, out)
+                assert relmax(host(out), want_P) < tol, (E, pick)
+
+
+def test_set_plan_rejects_what_the_kernels_cannot_run(G):
+    n, L = (16, 64), (4.0, 8.0)
+    with G.Context(n, L, 10.0, 0.3, I.harmonic(n, L), prec=G.GPE_FP64) as ctx:
+        for mode, axis, E, w in [(MODE_FP64, 0, 4, 1),      # E = 4 needs M >= 32 (nx = 16)
+                                 (MODE_FP64, 1, 8, 3),      # width not a power of two
+                                 (MODE_FP64, 1, 8, 64),     # 8 * 64 threads > 256
+                                 (MODE_FP64, 2, 8, 1),      # no z axis in 2D
+                                 (MODE_FP64, 0, 6, 1),      # E not 4 or 8
+                                 (MODE_C64, 0, 8, 1)]:      # no complex64 buffers in an FP64 context
+            with pytest.raises(G.GpeError):
+                ctx.set_plan(mode, axis, E, w)
+        ctx.set_plan(MODE_FP64, 1, 4, 8)
+        assert ctx.get_plan(MODE_FP64, 1) == (4, 8)
+
+
+def test_fp64_per_iterate_parity_with_E4_plans(G):
+    """The FP64 solver with E = 4 on both axes (graph loop) against the oracle's
+    iterates: same tolerances as the default plans."""
+    w = I.workload("c64_2d")
+    po = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    K = 20
+    _, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions(max_iter=K), keep_iterates=(K,))
+    with G.Context(w["n"], w["L"], w["eta"], w["omega"], w["V"], prec=G.GPE_FP64) as ctx:
+        ctx.set_plan(MODE_FP64, 0, 4, 4)
+        ctx.set_plan(MODE_FP64, 1, 4, 8)
+        phi = dev(w["phi0"])
+        o = G.solve_opts_default()
+        o.max_iter = K
+        o.use_graph = 1
+        rep = ctx.pcg_solve(phi, o, log_cap=64)
+    assert rep["iters"] == K and rep["loop_kind"] == 1
+    assert phase_aligned_rel_l2(host(phi), orep["iterates"][K]) < 1e-9
+    for n_ in range(K + 1):
+        e = orep["log"][n_]
+        assert abs(rep["log"][n_, 2] - e["E"]) <= 1e-12 * abs(e["E"]), n_
+        if n_ < K:
+            assert int(rep["log"][n_, 10]) == int(e["fallback"]) and int(rep["log"][n_, 11]) == e["backtracks"]
+
+
+@pytest.mark.parametrize("name", ["c64_2d", "fast256_2d"])
+def test_autotuned_mixed_solve(G, name):
+    """gpe_autotune on a mixed context, then the default solve: the chosen plans
+    are valid, the tuned iteration is not slower than the default one, the
+    process cache returns the same plans, and the answer passes the oracle."""
+    w = I.workload(name)
+    po = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    with G.Context(w["n"], w["L"], w["eta"], w["omega"], w["V"], prec=G.GPE_MIXED) as ctx:
+        rep_t = ctx.autotune(iters=10, use_cache=False)
+        assert not rep_t["cached"] and rep_t["candidates"] > 0
+        assert set(rep_t["plans"]) == {"complex64", "fp64", "refinement"}
+        for m in range(3):
+            assert 0 < rep_t["us_after"][m] <= rep_t["us_before"][m]
+        again = ctx.autotune(iters=10, use_cache=True)
+        assert again["cached"] and again["plans"] == rep_t["plans"]
+        for m, name_m in enumerate(("complex64", "fp64", "refinement")):
+            for ax, (E, wd) in enumerate(rep_t["plans"][name_m]):
+                assert ctx.get_plan(m, ax) == (E, wd)
+        phi = dev(w["phi0"])
+        rep = ctx.pcg_solve(phi, check=True)
+    assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
+    ph = host(phi)
+    lam = O.chemical_potential(po, ph)
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert abs(O.energy(po, ph) - rep["E"]) <= 1e-12 * abs(rep["E"])
+    if name == "c64_2d":
+        _, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions())
+        assert abs(rep["E"] - orep["E"]) <= 1e-7 * abs(orep["E"])
+
+
+def test_autotuned_batch_matches_its_single_solves(G):
+    """A batch tuned with gpe_batch_autotune reproduces single-instance solves
+    whose contexts were tuned through the same process cache."""
+    specs = [((64, 64), (8.0, 8.0), 100.0, 0.5, 1), ((32, 128), (6.0, 10.0), 60.0, 0.3, 2)]
+    ws = []
+    for n, L, eta, om, seed in specs:
+        ws.append(dict(n=n, L=L, eta=eta, omega=om, V=I.harmonic(n, L), prec=G.GPE_MIXED,
+                       phi0=I.perturbed(I.phi_d(n, L, om), seed, n, L)))
+    opts = G.solve_opts_default()
+    with G.Batch(ws) as B:
+        B.autotune(iters=5)
+        phis = [dev(w["phi0"]) for w in ws]
+        s, reps = B.solve(phis, opts)
+    assert s == G.GPE_OK
+    for i, w in enumerate(ws):
+        with G.Context(w["n"], w["L"], w["eta"], w["omega"], w["V"], prec=w["prec"]) as ctx:
+            assert ctx.autotune(iters=5)["cached"]
+            phi = dev(w["phi0"])
+            r1 = ctx.pcg_solve(phi, opts)
+        assert reps[i]["iters"] == r1["iters"] and reps[i]["E"] == r1["E"], (i, reps[i], r1)
+        assert np.array_equal(host(phis[i]), host(phi))
