@@ -37,10 +37,11 @@ WORKLOAD = "fast256_2d"
 METRIC = "ground states/sec to residual 1e-8 (256², 128³); H·φ GB/s vs HBM peak"
 UNIT = "ground_states/s"
 HPHI_BATCH = 512  # fields of 256x256 complex64 in the H phi roofline batch (268 MB in, 268 MB out)
-# DRAM bytes (read + write) of one cluster_apply_H<float,256> launch over HPHI_BATCH fields: an ncu
-# capture of a 256-field launch of the same kernel measured 134.5 MB + 91.4 MB; scaled by 512/256
-# fields (traffic grows in proportion to the fields).  Set to None when that kernel changes.
-HPHI_TRAFFIC_PER_LAUNCH = int(2 * (134.529536e6 + 91.378944e6))
+# DRAM bytes (read + write) of one cluster_apply_H_stream<float,256,16> launch over HPHI_BATCH
+# fields: an ncu capture of a 256-field launch of the same kernel measured 134.6 MB + 87.6 MB;
+# scaled by 512/256 fields (traffic grows in proportion to the fields).  Set to None when that
+# kernel changes.
+HPHI_TRAFFIC_PER_LAUNCH = int(2 * (134.565376e6 + 87.616256e6))
 
 
 def parse():
@@ -269,8 +270,8 @@ def main():
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
 
     # ---------------- roofline: H phi on a batch of fields larger than L2 ----------------
-    # HPHI_BATCH fields of the workload's grid, one thread-block cluster per field
-    # (gpe_apply_H_batch), complex64: algorithmic bytes = read phi + write H phi
+    # HPHI_BATCH fields of the workload's grid (gpe_apply_H_batch: resident 16-CTA clusters
+    # streaming over the fields), complex64: algorithmic bytes = read phi + write H phi
     # per point (16 B) + V once (4 B per grid point, shared by the batch).
     NB = HPHI_BATCH
     g = torch.Generator(device=dev).manual_seed(1)
@@ -384,7 +385,8 @@ def main():
                        "plans": tune and tune["plans"], "autotune_s": tune and tune["seconds"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": HPHI_TRAFFIC_PER_LAUNCH,
-                         "kernel": "cluster_apply_H<float,256> (gpe_apply_H_batch: one 16-CTA cluster per field)",
+                         "kernel": "cluster_apply_H_stream<float,256,16> (gpe_apply_H_batch: resident 16-CTA "
+                                   "clusters looping over the fields, next rows prefetched)",
                          "grid": f"{NB} x 256x256", "bytes_per_launch": hbytes,
                          "ms_per_launch": h_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},

@@ -70,6 +70,8 @@ struct gpe_ctx {
   PassPlan plan[3];      // default plan per axis (E = 8, heuristic widths)
   PassPlan mplan[3][3];  // plan used per launch mode [mode][axis] (the default, or the tuner's choice)
   int partials_cap = 0;  // blocks the reduction partials buffer holds
+  int hbatch_E = 8;      // values per thread of gpe_apply_H_batch's cluster kernel (plan mode 3):
+                         // 16 (streaming form) by default in single precision for n >= 64
   double vmax = 0.0;  // max V on the grid
   int max_threads[2] = {512, 256};
   bool warmed[3] = {false, false, false};  // per launch mode
@@ -310,6 +312,7 @@ extern "C" gpe_status gpe_create(const gpe_problem* prob, const double* V, void*
   }
   c->st = (cudaStream_t)stream;
   c->work = prob->prec == GPE_FP64 ? 1 : 0;
+  if (c->work == 0 && c->dim == 2 && c->n[0] == c->n[1] && c->n[0] >= 64 && c->n[0] <= 256) c->hbatch_E = 16;
   auto fail = [&](gpe_status s) { g_create_error = c->err; free_ctx(c); return s; };
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) { c->err = "stream create failed"; return fail(GPE_ERR_CUDA); }
 
@@ -403,6 +406,7 @@ extern "C" gpe_status gpe_apply_H_batch(gpe_ctx* c, int nbatch, const void* phi,
   a.eta = c->prob.eta; a.omega = c->prob.omega;
   a.xi = b.xi[0]; a.xiy = b.xi[1]; a.xc = b.xc[0]; a.yc = b.xc[1]; a.tw = b.tw[0]; a.V = b.V;
   a.phi = phi; a.f = f; a.out = out;
+  a.E = c->hbatch_E;
   GPE_CU(c, launch_cluster_apply_H(prec, a, c->st));
   return GPE_OK;
 }
@@ -931,8 +935,20 @@ static void plans_changed(gpe_ctx* c, int mode) {
   c->warmed[mode] = false;
 }
 
+static bool hbatch_eligible(const gpe_ctx* c) {
+  return c->dim == 2 && c->n[0] == c->n[1] && c->n[0] >= 32 && c->n[0] <= 256;
+}
+
 extern "C" gpe_status gpe_set_plan(gpe_ctx* c, int mode, int axis, int E, int width) {
   if (!c) return GPE_ERR_ARG;
+  if (mode == 3) {  // the cluster kernel of gpe_apply_H_batch: E only, width = rows per CTA
+    const bool ok = hbatch_eligible(c) && axis == 0 && width == 16 &&
+                    (E == 8 || (E == 16 && c->work == 0 && c->n[0] >= 64));
+    if (!ok) { c->err = "plan not supported by the batched H kernel"; return GPE_ERR_ARG; }
+    GPE_CU(c, cudaStreamSynchronize(c->st));
+    c->hbatch_E = E;
+    return GPE_OK;
+  }
   if (!mode_available(c, mode)) { c->err = "launch mode not used by this context"; return GPE_ERR_ARG; }
   PassPlan pl;
   if (!make_plan(c, mode, axis, E, width, pl)) { c->err = "plan not supported for this grid and mode"; return GPE_ERR_ARG; }
@@ -943,6 +959,11 @@ extern "C" gpe_status gpe_set_plan(gpe_ctx* c, int mode, int axis, int E, int wi
 }
 
 extern "C" gpe_status gpe_get_plan(const gpe_ctx* c, int mode, int axis, int* E, int* width) {
+  if (c && E && width && mode == 3 && axis == 0 && hbatch_eligible(c)) {
+    *E = c->hbatch_E;
+    *width = 16;
+    return GPE_OK;
+  }
   if (!c || !E || !width || mode < 0 || mode > 2 || axis < 0 || axis >= c->dim) return GPE_ERR_ARG;
   const PassPlan& pl = c->mplan[mode][axis];
   *E = pl.E;

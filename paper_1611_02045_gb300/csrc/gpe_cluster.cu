@@ -7,18 +7,37 @@ namespace gpe {
 cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStream_t st) {
   if (is_double) {
     switch (a.M) {
-      case 32: return launch_cluster_apply_H_one<double, 32>(a, st);
-      case 64: return launch_cluster_apply_H_one<double, 64>(a, st);
-      case 128: return launch_cluster_apply_H_one<double, 128>(a, st);
-      case 256: return launch_cluster_apply_H_one<double, 256>(a, st);
+      case 32: return launch_cluster_apply_H_one<double, 32, 8>(a, st);
+      case 64: return launch_cluster_apply_H_one<double, 64, 8>(a, st);
+      case 128: return launch_cluster_apply_H_one<double, 128, 8>(a, st);
+      case 256: return launch_cluster_apply_H_one<double, 256, 8>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (a.E == 16) {
+    // single precision, E = 16: the streaming (persistent, prefetching) form
+    // when the fields are 16-byte aligned, else one field per cluster
+    bool ok = false;
+    cudaError_t e = cudaSuccess;
+    switch (a.M) {
+      case 64: e = launch_cluster_apply_H_stream<float, 64, 16>(a, st, &ok); break;
+      case 128: e = launch_cluster_apply_H_stream<float, 128, 16>(a, st, &ok); break;
+      case 256: e = launch_cluster_apply_H_stream<float, 256, 16>(a, st, &ok); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess || ok) return e;
+    switch (a.M) {
+      case 64: return launch_cluster_apply_H_one<float, 64, 16>(a, st);
+      case 128: return launch_cluster_apply_H_one<float, 128, 16>(a, st);
+      case 256: return launch_cluster_apply_H_one<float, 256, 16>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (a.M) {
-    case 32: return launch_cluster_apply_H_one<float, 32>(a, st);
-    case 64: return launch_cluster_apply_H_one<float, 64>(a, st);
-    case 128: return launch_cluster_apply_H_one<float, 128>(a, st);
-    case 256: return launch_cluster_apply_H_one<float, 256>(a, st);
+    case 32: return launch_cluster_apply_H_one<float, 32, 8>(a, st);
+    case 64: return launch_cluster_apply_H_one<float, 64, 8>(a, st);
+    case 128: return launch_cluster_apply_H_one<float, 128, 8>(a, st);
+    case 256: return launch_cluster_apply_H_one<float, 256, 8>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -39,16 +39,28 @@ struct ClusterHArgs {
   const void* phi;   // density fields
   const void* f;     // operands (may equal phi)
   void* out;         // results
+  int E;             // values per thread: 16 (single precision, M >= 64) or 8 (also when 0)
 };
 
 // Two CTAs per SM in single precision (two fields in flight per SM group).
 template <typename T> struct ClusterMinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
-template <typename T, int M>
-__global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::value) cluster_apply_H(ClusterHArgs a) {
+// Shared memory per CTA: operand rows, accumulator rows, and the exchange
+// buffer (rows of the x part or columns of the y part, padded).
+template <typename T, int M> struct ClusterHSmem {
+  static constexpr int LS = M + M / 16;  // padded line stride
+  static constexpr size_t bytes = (size_t)(2 * kClusterRows * M + kClusterRows * LS) * sizeof(cplx<T>);
+};
+
+// EV values per thread: 8 (radix-8 then 8/4/2 Stockham stages, two exchanges
+// per 256-point transform) or 16 (radix-16 stages: one exchange, half the
+// shared-memory traffic, half the threads).
+template <typename T, int M, int EV>
+__global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::value) cluster_apply_H(ClusterHArgs a) {
   using C = cplx<T>;
-  constexpr int E = 8, Tl = M / 8, R = kClusterRows;
-  constexpr int LS = M + M / 16;
+  constexpr int E = EV, Tl = M / EV, R = kClusterRows;
+  constexpr int LS = ClusterHSmem<T, M>::LS;
+  static_assert(Tl <= 32 && (32 % Tl) == 0, "a row's threads lie inside one warp");
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int csize = (int)cl.num_blocks();
@@ -63,7 +75,8 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::v
   const T om = T(a.omega);
   const long long fb = field * a.stride;
 
-  // ---- x part, rows of this CTA -------------------------------------------------
+  // ---- x part, rows of this CTA: row l is transformed by the Tl threads
+  //      t + Tl l, inside one warp, in its own exchange row (warp barriers) ----
   {
     const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
     const int y = rank * R + l;
@@ -83,14 +96,14 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::v
       fs[l * M + x] = w[q];
     }
     auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
-    line_dft<M, E, -1>(w, xs, si, t, tw);
+    line_dft<M, E, -1, true>(w, xs, si, t, tw);
     const T yy = static_cast<const T*>(a.yc)[y];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const T k = xi[t + q * Tl];
       w[q] = cscale(w[q], (T(0.5) * k * k + om * yy * k) * invM);
     }
-    line_dft<M, E, +1>(w, xs, si, t, tw);
+    line_dft<M, E, +1, true>(w, xs, si, t, tw);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const C v = fs[l * M + t + q * Tl];  // the operand, kept in shared memory
@@ -110,9 +123,8 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::v
       const C* src = cl.map_shared_rank(fs, (unsigned)(y / R));
       w[q] = src[(y % R) * M + x];
     }
-    __syncthreads();  // the x part's readers of xs are done (line_dft syncs again before writing)
     auto si = [c](int pos) { return pos * R + c; };
-    line_dft<M, E, -1>(w, xs, si, t, tw);
+    line_dft<M, E, -1>(w, xs, si, t, tw);  // its first barrier also retires the x part's use of xs
     const T xx = static_cast<const T*>(a.xc)[x];
     const T* __restrict__ xiy = static_cast<const T*>(a.xiy);
 #pragma unroll
@@ -144,14 +156,139 @@ __global__ void __launch_bounds__((M / 8) * kClusterRows, ClusterMinBlocks<T>::v
   }
 }
 
-template <typename T, int M>
-cudaError_t launch_cluster_apply_H_one(const ClusterHArgs& a, cudaStream_t st) {
+// 16-byte asynchronous copy global -> shared (cached in L2 only) and its group
+// control (cp.async, sm_80 and later).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Streaming form of the batched H phi: each resident cluster loops over the
+// fields cluster_id, cluster_id + #clusters, ...; while the columns of field k
+// are transformed, the rows of field k + #clusters are already being copied
+// into the second row buffer.  The x part stores t = A_x f + (V + eta|phi|^2) f
+// straight to out; the y part adds its columns' A_y f into out (the lines are
+// still in L2), so no accumulator rows are kept and one cluster barrier per
+// field suffices:
+//   wait rows(k) -> x part(k) -> cluster barrier -> prefetch rows(k+1)
+//   -> y part(k) [gathers rows(k) from the cluster]
+// After the barrier of field k every CTA has finished the y part of field
+// k - 1, so the buffer that held rows(k - 1) is free for rows(k + 1).
+// Requires f (and phi) 16-byte aligned.
+template <typename T, int M, int EV>
+__global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::value)
+    cluster_apply_H_stream(ClusterHArgs a) {
   using C = cplx<T>;
+  constexpr int E = EV, Tl = M / EV, R = kClusterRows, LS = M + M / 16;
+  constexpr int NT = Tl * R;  // threads per CTA
+  static_assert(Tl <= 32 && (32 % Tl) == 0, "a row's threads lie inside one warp");
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int csize = (int)cl.num_blocks();
+  const long long cid = blockIdx.x / csize, ncl = gridDim.x / csize;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* rows = reinterpret_cast<C*>(smraw);  // [2][R][M] row buffers
+  C* xs = rows + 2 * R * M;                // [R][LS] (x) or [M][R] (y) exchange
+  const C* __restrict__ f = static_cast<const C*>(a.f);
+  const C* __restrict__ phi = static_cast<const C*>(a.phi);
+  const T* __restrict__ V = static_cast<const T*>(a.V);
+  C* out = static_cast<C*>(a.out);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const T* __restrict__ xi = static_cast<const T*>(a.xi);
+  const T* __restrict__ xiy = static_cast<const T*>(a.xiy);
+  const T invM = T(1) / T(M);
+  const T om = T(a.omega), eta = T(a.eta);
+  const bool same = (a.f == a.phi);
+
+  // rows 16 rank .. 16 rank + 15 of field fld: R M contiguous elements
+  auto fetch = [&](long long fld, C* dst) {
+    const char* src = reinterpret_cast<const char*>(f + fld * a.stride + (long long)rank * R * M);
+    char* d = reinterpret_cast<char*>(dst);
+    constexpr int chunks = R * M * (int)sizeof(C) / 16;
+    for (int i = threadIdx.x; i < chunks; i += NT) cp_async16(d + 16 * i, src + 16 * (long long)i);
+    cp_async_commit();
+  };
+  if (cid < a.nbatch) fetch(cid, rows);
+  int k = 0;
+  for (long long fld = cid; fld < a.nbatch; fld += ncl, ++k) {
+    C* fs = rows + (k & 1) * R * M;
+    C* fn = rows + ((k & 1) ^ 1) * R * M;
+    cp_async_wait_all();
+    __syncthreads();  // rows(k) complete in fs; every warp is done with xs (y part of k - 1)
+    const long long fb = fld * a.stride;
+
+    // ---- x part: row l by the Tl threads t + Tl l (one warp, warp barriers) ----
+    {
+      const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
+      const int y = rank * R + l;
+      C w[E];
+      T m[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int x = t + q * Tl;
+        w[q] = fs[l * M + x];
+        const C ph = same ? w[q] : phi[fb + (long long)y * M + x];
+        m[q] = V[(long long)y * M + x] + eta * (ph.x * ph.x + ph.y * ph.y);
+      }
+      auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
+      line_dft<M, E, -1, true>(w, xs, si, t, tw);
+      const T yy = static_cast<const T*>(a.yc)[y];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const T kx = xi[t + q * Tl];
+        w[q] = cscale(w[q], (T(0.5) * kx * kx + om * yy * kx) * invM);
+      }
+      line_dft<M, E, +1, true>(w, xs, si, t, tw);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int x = t + q * Tl;
+        const C v = fs[l * M + x];
+        out[fb + (long long)y * M + x] = cmk<C>(w[q].x + m[q] * v.x, w[q].y + m[q] * v.y);
+      }
+    }
+    cl.sync();  // rows(k) of every CTA visible; t rows stored; y parts of k - 1 finished
+    if (fld + ncl < a.nbatch) fetch(fld + ncl, fn);
+
+    // ---- y part: columns 16 rank .. 16 rank + 15, rows gathered from the cluster ----
+    {
+      const int c = threadIdx.x % R, t = threadIdx.x / R;
+      const int x = rank * R + c;
+      C w[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int y = t + q * Tl;
+        const C* src = cl.map_shared_rank(fs, (unsigned)(y / R));
+        w[q] = src[(y % R) * M + x];
+      }
+      auto si = [c](int pos) { return pos * R + c; };
+      line_dft<M, E, -1>(w, xs, si, t, tw);  // its first barrier retires the x part's use of xs
+      const T xx = static_cast<const T*>(a.xc)[x];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const T ky = xiy[t + q * Tl];
+        w[q] = cscale(w[q], (T(0.5) * ky * ky - om * xx * ky) * invM);
+      }
+      line_dft<M, E, +1>(w, xs, si, t, tw);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const long long g = fb + (long long)(t + q * Tl) * M + x;
+        const C o = __ldcg(&out[g]);  // t, stored by the row's owner before the barrier
+        out[g] = cadd(o, w[q]);
+      }
+    }
+  }
+  cl.sync();  // no CTA leaves while others may still gather from its rows
+}
+
+template <typename T, int M, int EV>
+cudaError_t launch_cluster_apply_H_one(const ClusterHArgs& a, cudaStream_t st) {
   constexpr int R = kClusterRows;
   const int csize = M / R;
-  const int threads = (M / 8) * R;
-  const size_t smem = (size_t)(2 * R * M + R * (M + M / 16)) * sizeof(C);
-  auto kern = cluster_apply_H<T, M>;
+  const int threads = (M / EV) * R;
+  const size_t smem = ClusterHSmem<T, M>::bytes;
+  auto kern = cluster_apply_H<T, M, EV>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -174,6 +311,49 @@ cudaError_t launch_cluster_apply_H_one(const ClusterHArgs& a, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// Streaming launcher: as many clusters as can be resident (at most one per
+// field); false in *ok when the kernel cannot be used (f or phi not 16-byte
+// aligned), so the caller launches the one-field-per-cluster form.
+template <typename T, int M, int EV>
+cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st, bool* ok) {
+  *ok = false;
+  if ((reinterpret_cast<uintptr_t>(a.f) & 15u) != 0 || (reinterpret_cast<uintptr_t>(a.phi) & 15u) != 0) return cudaSuccess;
+  constexpr int R = kClusterRows;
+  const int csize = M / R;
+  const int threads = (M / EV) * R;
+  const size_t smem = (size_t)(2 * R * M + R * (M + M / 16)) * sizeof(cplx<T>);
+  auto kern = cluster_apply_H_stream<T, M, EV>;
+  static int max_clusters = -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (max_clusters < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (csize > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    int n = 0;
+    cfg.gridDim = dim3((unsigned)csize);
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess || n < 1) { cudaGetLastError(); n = 1; }
+    max_clusters = n;
+  }
+  const int ncl = a.nbatch < max_clusters ? a.nbatch : max_clusters;
+  cfg.gridDim = dim3((unsigned)(ncl * csize));
+  *ok = true;
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 

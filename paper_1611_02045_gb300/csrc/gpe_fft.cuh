@@ -115,11 +115,25 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dft_small(
   }
 }
 
+// Lanes of the calling warp that exist in this (1D) block.
+__device__ __forceinline__ unsigned block_warp_mask() {
+  const unsigned n = blockDim.x - (threadIdx.x & ~31u);
+  return n >= 32u ? 0xffffffffu : ((1u << n) - 1u);
+}
+
+// Barrier between exchange stages.  WARP: every line's threads lie inside one
+// warp and its shared-memory slots belong to that line alone, so the warp's
+// own barrier (which also orders its shared-memory accesses) is enough.
+template <bool WARP> __device__ __forceinline__ void line_sync() {
+  if constexpr (WARP) __syncwarp(block_warp_mask());
+  else __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Stockham stages.  SI: functor mapping a line position to a shared-memory
 // element index for this thread's line slot.
 // ---------------------------------------------------------------------------
-template <int M, int E, int NS, int DIR, typename C, typename SI>
+template <int M, int E, int NS, int DIR, bool WARP, typename C, typename SI>
 __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
   constexpr int Tl = M / E;
   constexpr int R = (M / NS >= E) ? E : (M / NS);
@@ -140,7 +154,7 @@ __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t
     for (int r = 0; r < R; ++r) v[b + r * NB] = x[r];
   }
   if constexpr (NS * R < M) {
-    __syncthreads();  // previous readers of sm are done
+    line_sync<WARP>();  // previous readers of sm are done
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = t + b * Tl;
@@ -149,19 +163,19 @@ __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t
 #pragma unroll
       for (int r = 0; r < R; ++r) sm[si(base + r * NS)] = v[b + r * NB];
     }
-    __syncthreads();
+    line_sync<WARP>();
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = sm[si(t + q * Tl)];
-    fft_stages<M, E, NS * R, DIR>(v, sm, si, t, tw);
+    fft_stages<M, E, NS * R, DIR, WARP>(v, sm, si, t, tw);
   }
 }
 
 // Forward (DIR = -1) or inverse-unnormalised (DIR = +1) DFT of one line held
 // as v[q] = f[t + q*Tl]; on return v[q] = F[f][t + q*Tl].  Every thread of the
-// block must call it (it contains __syncthreads()).
-template <int M, int E, int DIR, typename C, typename SI>
+// block (WARP: of the warp) must call it: it contains the stage barriers.
+template <int M, int E, int DIR, bool WARP = false, typename C, typename SI>
 __device__ __forceinline__ void line_dft(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
-  fft_stages<M, E, 1, DIR>(v, sm, si, t, tw);
+  fft_stages<M, E, 1, DIR, WARP>(v, sm, si, t, tw);
 }
 
 }  // namespace gpe

@@ -404,6 +404,9 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
   using CD = cplx<TD>;
   constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
   constexpr int LS = M + M / 16;  // padded line stride in shared memory
+  // lines of at most 32 threads lie inside one warp (tid = t + Tl l) and own
+  // their shared-memory rows: their transforms need only warp barriers
+  constexpr bool W = Tl <= 32;
   CF* sm = reinterpret_cast<CF*>(smraw);
 
   const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
@@ -442,7 +445,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       vv[q] = V[g];
       v[q] = cconv<TF>((a.f && !a.solver) ? f[g] : x);
     }
-    line_dft<M, E, -1>(v, sm, si, t, tw);
+    line_dft<M, E, -1, W>(v, sm, si, t, tw);
     const TF y = tab<TF>(a.xc[1])[iy];
     const TF om = TF(a.omega);
     TF akin = 0, arot = 0;  // arot: the rotation symbol without omega (omega is applied in finalize_H)
@@ -454,7 +457,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       akin += mk * a2; arot += kr * a2;
       v[q] = cscale(v[q], (mk + om * kr) * invM);
     }
-    line_dft<M, E, +1>(v, sm, si, t, tw);
+    line_dft<M, E, +1, W>(v, sm, si, t, tw);
     CS* __restrict__ tout = static_cast<CS*>(a.t);
     const TS eta = TS(a.eta);
     TS apot = 0, au2 = 0, an2 = 0, umax = 0;
@@ -493,7 +496,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       rmax = fmax(rmax, a2); r2 += a2;
       v[q] = cconv<TF>(cscale(r, TS(1) / sqrt(den)));
     }
-    line_dft<M, E, -1>(v, sm, si, t, tw);
+    line_dft<M, E, -1, W>(v, sm, si, t, tw);
     CD* __restrict__ sout = static_cast<CD*>(a.s);
 #pragma unroll
     for (int q = 0; q < E; ++q) sout[base + t + q * Tl] = cconv<TD>(v[q]);
@@ -509,7 +512,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     const TS alpha = TS(S.alpha);
     const TS eta = TS(a.eta);
     if (!a.solver) {
-      line_dft<M, E, +1>(v, sm, si, t, tw);
+      line_dft<M, E, +1, W>(v, sm, si, t, tw);
       CD* __restrict__ out = static_cast<CD*>(a.out);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
@@ -537,7 +540,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       pp[q] = pprev[g];
       vv[q] = V[g];
     }
-    line_dft<M, E, +1>(v, sm, si, t, tw);
+    line_dft<M, E, +1, W>(v, sm, si, t, tw);
     const TS lam = TS(S.lam);
     TS a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
@@ -584,7 +587,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       aV += V[g] * wq;
       aW1 += wq; aUV += u * vr; aV2 += vr * vr; aUW += u * wq; aVW += vr * wq; aW2 += wq * wq; aRho += vr;
     }
-    line_dft<M, E, -1>(v, sm, si, t, tw);
+    line_dft<M, E, -1, W>(v, sm, si, t, tw);
     const TF y = tab<TF>(a.xc[1])[iy];
     const TF om = TF(a.omega);
     TF akr = 0;

@@ -22,12 +22,15 @@ def main():
     ap.add_argument("--prec", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--op", choices=["apply_H", "apply_H_batch", "precond", "energy", "solve"], default="apply_H")
     ap.add_argument("--batch", type=int, default=64, help="fields for --op apply_H_batch (2D grid)")
+    ap.add_argument("--hbatch-E", type=int, default=0, help="values per thread of the batched H kernel (8, 16)")
     ap.add_argument("--workload", default="fast256_2d", help="for --op solve")
     ap.add_argument("--max-iter", type=int, default=50, help="for --op solve")
     ap.add_argument("--switch-res", type=float, default=0.0, help="for --op solve (mixed)")
     ap.add_argument("--loop", choices=["default", "cluster", "persistent", "graph", "host"], default="default",
                     help="for --op solve: the library default, the cluster-resident complex64 phase, the "
                          "persistent kernel, the graph with a device-side loop, or a host loop")
+    ap.add_argument("--autotune", action="store_true", help="for --op solve: tune the pass-kernel plans first")
+    ap.add_argument("--plan", default="", help="for --op solve: E,width applied to every mode and axis")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -43,6 +46,13 @@ def main():
     if a.op == "solve":
         w = I.workload(a.workload)
         ctx = gpe.Context(w["n"], w["L"], w["eta"], w["omega"], w["V"], prec=prec)
+        if a.autotune:
+            ctx.autotune(iters=20)
+        if a.plan:
+            E, wd = (int(v) for v in a.plan.split(","))
+            for m in ((0, 1, 2) if prec == gpe.GPE_MIXED else (1,)):
+                for ax in range(len(w["n"])):
+                    ctx.set_plan(m, ax, E, wd)
         phi0 = torch.from_numpy(w["phi0"].copy()).to(dev)
         phi = torch.empty_like(phi0)
         opts = gpe.solve_opts_default()
@@ -72,6 +82,8 @@ def main():
     V = torch.zeros(N, dtype=torch.float64, device=dev)
     ctx = gpe.Context(n, L, 100.0, 0.5, V, prec=prec)
     del V
+    if a.hbatch_E:
+        ctx.set_plan(3, 0, a.hbatch_E, 16)
     dt = torch.complex128 if a.prec == "fp64" else torch.complex64
     g = torch.Generator(device=dev).manual_seed(1)
     nf = a.batch if a.op == "apply_H_batch" else 1

@@ -180,3 +180,76 @@ def test_autotuned_batch_matches_its_single_solves(G):
             r1 = ctx.pcg_solve(phi, opts)
         assert reps[i]["iters"] == r1["iters"] and reps[i]["E"] == r1["E"], (i, reps[i], r1)
         assert np.array_equal(host(phis[i]), host(phi))
+
+
+@pytest.mark.parametrize("M", [64, 128, 256])
+@pytest.mark.parametrize("E", [8, 16])
+def test_batched_H_kernel_plans_match_oracle(G, M, E):
+    """gpe_apply_H_batch's cluster kernel with E = 8 and E = 16 values per thread
+    (plan mode 3) on a batch of complex64 fields against the oracle."""
+    n, L = (M, M), (8.0, 8.0)
+    V = I.harmonic(n, L)
+    eta, om = 37.0, 0.7
+    po = O.Problem(n, L, eta, om, V)
+    nb = 5
+    phis = np.stack([I.random_field(10 + b, n, L) for b in range(nb)])
+    fs = np.stack([I.random_field(20 + b, n, L) for b in range(nb)])
+    ph_d, f_d = dev(phis, torch.complex64), dev(fs, torch.complex64)
+    out = torch.empty_like(f_d)
+    with G.Context(n, L, eta, om, V, prec=G.GPE_MIXED) as ctx:
+        ctx.set_plan(3, 0, E, 16)
+        assert ctx.get_plan(3, 0) == (E, 16)
+        ctx.apply_H_batch(nb, ph_d, f_d, out)
+        got = host(out)
+    phh, fh = host(ph_d), host(f_d)
+    for b in range(nb):
+        assert relmax(got[b], O.apply_H(po, phh[b], fh[b])) < 2e-5, b
+
+
+@pytest.mark.parametrize("M,nb", [(64, 150), (256, 37)])
+def test_streaming_batched_H_kernel_loops_over_fields(G, M, nb):
+    """With E = 16 and 16-byte aligned fields the batched H kernel runs as
+    resident clusters looping over the fields (rows of the next field copied
+    while the current one's columns are transformed): more fields than
+    resident clusters, every field against the oracle; phi != f."""
+    n, L = (M, M), (8.0, 8.0)
+    V = I.harmonic(n, L) + 0.2 * I.smooth_bumps(n, L, 3)
+    eta, om = 41.0, 0.6
+    po = O.Problem(n, L, eta, om, V)
+    phis = np.stack([I.random_field(100 + b, n, L) for b in range(nb)])
+    fs = np.stack([I.random_field(300 + b, n, L) for b in range(nb)])
+    ph_d, f_d = dev(phis, torch.complex64), dev(fs, torch.complex64)
+    out = torch.empty_like(f_d)
+    with G.Context(n, L, eta, om, V, prec=G.GPE_MIXED) as ctx:
+        ctx.set_plan(3, 0, 16, 16)
+        for rep in range(2):  # twice: the second launch starts from the first one's buffers
+            out.fill_(float("nan"))
+            ctx.apply_H_batch(nb, ph_d, f_d, out)
+            got = host(out)
+            assert np.isfinite(got).all()
+    phh, fh = host(ph_d), host(f_d)
+    for b in range(nb):
+        assert relmax(got[b], O.apply_H(po, phh[b], fh[b])) < 2e-5, b
+
+
+def test_batched_H_kernel_falls_back_for_misaligned_fields(G):
+    """Fields that do not start on a 16-byte boundary cannot be copied by the
+    streaming form's 16-byte asynchronous copies: the one-field-per-cluster
+    form runs instead, with the same results."""
+    M, nb = 128, 20
+    n, L = (M, M), (8.0, 8.0)
+    V = I.harmonic(n, L)
+    po = O.Problem(n, L, 30.0, 0.5, V)
+    fs = np.stack([I.random_field(500 + b, n, L) for b in range(nb)])
+    buf = torch.empty(nb * M * M + 1, dtype=torch.complex64, device="cuda")
+    f_d = buf[1:]  # 8 bytes past a 256-byte boundary
+    f_d.copy_(torch.from_numpy(fs.reshape(-1).astype(np.complex64)))
+    assert f_d.data_ptr() % 16 == 8
+    out = torch.empty_like(f_d)
+    with G.Context(n, L, 30.0, 0.5, V, prec=G.GPE_MIXED) as ctx:
+        assert ctx.get_plan(3, 0) == (16, 16)  # the default in single precision
+        ctx.apply_H_batch(nb, f_d, f_d, out)
+        got = host(out).reshape(nb, M, M)
+    fh = host(f_d).reshape(nb, M, M)
+    for b in range(nb):
+        assert relmax(got[b], O.apply_H(po, fh[b], fh[b])) < 2e-5, b
