@@ -44,6 +44,36 @@ template <int DIR, typename C> __device__ __forceinline__ C ctw(C a, C w) {
                  : cmk<C>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
 }
 
+// Packed two-wide single precision (add / sub / mul .rn.f32x2, GB300): one
+// instruction per complex add, subtract or real scaling of a float2, each
+// lane rounded as the scalar .rn operation.  These overloads take precedence
+// over the generic templates above for complex64 values.
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a.x, a.y)), "l"(f2_pack(b.x, b.y)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a.x, a.y)), "l"(f2_pack(b.x, b.y)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a.x, a.y)), "l"(f2_pack(s, s)));
+  return f2_unpack(d);
+}
+
 // Twiddle loads through the read-only path where the type allows it.
 __device__ __forceinline__ float2 ld_tw(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
