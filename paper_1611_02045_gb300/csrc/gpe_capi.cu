@@ -807,7 +807,7 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
     GPE_CU(c, cudaMemsetAsync(b.r_prev, 0, sbytes, c->st));
   }
   GPE_CU(c, cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
-  GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->st));
+  GPE_CU(c, launch_init_norm(b.tab_h, b.phi, c->N, c->weight, c->ctl_solve, c->partials, c->ticket, c->st));
   bool done_launch = false;
   int loop = o.use_graph ? 1 : 0;
   if (o.use_graph == 3 && mode == 0 && c->dim == 2 && c->n[0] == c->n[1] && c->n[0] >= 32 && c->n[0] <= 256) {
@@ -996,7 +996,7 @@ static gpe_status tune_time(gpe_ctx* c, int mode, int iters, const std::vector<d
     if (e == cudaSuccess) e = cudaMemsetAsync(b.p, 0, (b.tab_d ? 16 : 8) * (size_t)N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.r_prev, 0, (b.tab_h ? 16 : 8) * (size_t)N, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl_solve, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_init_norm(b.tab_h, b.phi, N, c->weight, c->ctl_solve, st);
+    if (e == cudaSuccess) e = launch_init_norm(b.tab_h, b.phi, N, c->weight, c->ctl_solve, c->partials, c->ticket, st);
     if (e != cudaSuccess) { c->err = std::string("tuner set-up: ") + cudaGetErrorString(e); s = GPE_ERR_CUDA; break; }
     for (int k = 0; k < 2 && s == GPE_OK; ++k) s = enqueue_iteration(c, mode, st, 0ull);
     if (s != GPE_OK) break;
@@ -1255,7 +1255,7 @@ static gpe_status batch_enqueue(gpe_batch* B, gpe_ctx* c, Ctl* ctl_init) {
   if (c->prob.prec != GPE_MIXED) {
     const IterBufs b1 = iter_bufs(c, 1);
     if ((s = clear_dir(b1)) != GPE_OK) return s;
-    GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, st));
+    GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, c->partials, c->ticket, st));
     cudaGraphConditionalHandle h;
     if ((s = new_handle(B, 1, &h)) != GPE_OK) return s;
     return capture_while(B, c, 1, h);
@@ -1263,7 +1263,7 @@ static gpe_status batch_enqueue(gpe_batch* B, gpe_ctx* c, Ctl* ctl_init) {
   const IterBufs b0 = iter_bufs(c, 0);
   GPE_CU(B, launch_convert_c128_to_c64(c->pb[1].phi, c->pb[0].phi, N, st));
   if ((s = clear_dir(b0)) != GPE_OK) return s;
-  GPE_CU(B, launch_init_norm(b0.tab_h, b0.phi, N, c->weight, c->ctl_solve, st));
+  GPE_CU(B, launch_init_norm(b0.tab_h, b0.phi, N, c->weight, c->ctl_solve, c->partials, c->ticket, st));
   if (cluster_eligible(c)) {
     ClusterSolveArgs P;
     std::memset(&P, 0, sizeof(P));
@@ -1280,7 +1280,7 @@ static gpe_status batch_enqueue(gpe_batch* B, gpe_ctx* c, Ctl* ctl_init) {
   const IterBufs b2 = iter_bufs(c, 2);
   GPE_CU(B, launch_batch_between(c->pb[0].phi, c->pb[1].phi, c->pb[2].phi, N, c->ctl_solve, st));
   if ((s = clear_dir(b2)) != GPE_OK) return s;
-  GPE_CU(B, launch_init_norm(b2.tab_h, b2.phi, N, c->weight, c->ctl_solve, st));
+  GPE_CU(B, launch_init_norm(b2.tab_h, b2.phi, N, c->weight, c->ctl_solve, c->partials, c->ticket, st));
   cudaGraphConditionalHandle h2;
   if ((s = new_handle(B, 0, &h2)) != GPE_OK) return s;
   GPE_CU(B, launch_batch_gate(c->ctl_solve, (unsigned long long)h2, st));
@@ -1289,7 +1289,7 @@ static gpe_status batch_enqueue(gpe_batch* B, gpe_ctx* c, Ctl* ctl_init) {
   // FP64 completion when the refinement stalled
   const IterBufs b1 = iter_bufs(c, 1);
   if ((s = clear_dir(b1)) != GPE_OK) return s;
-  GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, st));
+  GPE_CU(B, launch_init_norm(b1.tab_h, b1.phi, N, c->weight, c->ctl_solve, c->partials, c->ticket, st));
   cudaGraphConditionalHandle h3;
   if ((s = new_handle(B, 0, &h3)) != GPE_OK) return s;
   GPE_CU(B, launch_batch_gate64(c->ctl_solve, (unsigned long long)h3, st));

@@ -152,7 +152,9 @@ cudaError_t launch_convert_ds_to_c128(const void* src, void* dst, long long n, c
 // ctl->c = 1, s = 0, inv_nrm = 1 / ||phi||, retract = 1 (weighted norm), so
 // that the next H pass normalises phi in place.
 // prec: 0 complex64, 1 complex128, 2 double-single.
-cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st);
+// partials: >= 1024 doubles of scratch; ticket: the reduction ticket (0 on entry, 0 on exit).
+cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, double* partials,
+                             unsigned* ticket, cudaStream_t st);
 // Tangent-space adjoint solve (gpe_adjoint.cu): device scalars of the
 // projected conjugate gradient iteration, and its kernels.  Each reduction
 // launcher sums weighted inner products into S and runs the scalar step

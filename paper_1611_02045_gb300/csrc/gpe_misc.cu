@@ -222,12 +222,19 @@ cudaError_t launch_batch_final(const void* phids, void* phi128, long long n, con
   return cudaGetLastError();
 }
 
-// One block, fixed-order FP64 sum of |phi|^2 (runs once per solve phase).
+// Fixed-order FP64 sum of |phi|^2 over all blocks (runs once per solve
+// phase): per-block partials, the last block to finish sums them in block
+// order and arms the control block: c = 1, s = 0, inv_nrm = 1 / ||phi||,
+// retract = 1, so that the next H pass normalises phi in place.
+constexpr int kNormThreads = 256;
 template <typename C>
-__global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, long long n, double weight, Ctl* ctl) {
-  __shared__ double sm[32];
+__global__ void __launch_bounds__(kNormThreads) k_init_norm(const C* __restrict__ phi, long long n, double weight,
+                                                            Ctl* ctl, double* __restrict__ partials,
+                                                            unsigned* ticket) {
+  __shared__ double sm[kNormThreads / 32];
+  __shared__ int s_last;
   double acc = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const C v = phi[i];
     const double re = (double)v.x, im = (double)v.y;
     acc += re * re + im * im;
@@ -236,20 +243,34 @@ __global__ void __launch_bounds__(1024) k_init_norm(const C* __restrict__ phi, l
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sm[w];
-    ctl->c = 1.0;
-    ctl->s = 0.0;
-    ctl->inv_np = 0.0;
-    ctl->inv_nrm = 1.0 / sqrt(weight * tot);
-    ctl->retract = 1;
+    double b = 0.0;
+    for (int w = 0; w < kNormThreads / 32; ++w) b += sm[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
   }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(partials + b);
+  ctl->c = 1.0;
+  ctl->s = 0.0;
+  ctl->inv_np = 0.0;
+  ctl->inv_nrm = 1.0 / sqrt(weight * tot);
+  ctl->retract = 1;
+  *ticket = 0u;  // ready for the next reduction
 }
 
-cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, cudaStream_t st) {
-  if (prec == 1) k_init_norm<double2><<<1, 1024, 0, st>>>((const double2*)phi, n, weight, ctl);
-  else if (prec == 2) k_init_norm<dsc><<<1, 1024, 0, st>>>((const dsc*)phi, n, weight, ctl);
-  else k_init_norm<float2><<<1, 1024, 0, st>>>((const float2*)phi, n, weight, ctl);
+cudaError_t launch_init_norm(int prec, const void* phi, long long n, double weight, Ctl* ctl, double* partials,
+                             unsigned* ticket, cudaStream_t st) {
+  long long g = (n + 8LL * kNormThreads - 1) / (8LL * kNormThreads);
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  const int grid = (int)g;
+  if (prec == 1) k_init_norm<double2><<<grid, kNormThreads, 0, st>>>((const double2*)phi, n, weight, ctl, partials, ticket);
+  else if (prec == 2) k_init_norm<dsc><<<grid, kNormThreads, 0, st>>>((const dsc*)phi, n, weight, ctl, partials, ticket);
+  else k_init_norm<float2><<<grid, kNormThreads, 0, st>>>((const float2*)phi, n, weight, ctl, partials, ticket);
   return cudaGetLastError();
 }
 

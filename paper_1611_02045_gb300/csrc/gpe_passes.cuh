@@ -632,8 +632,12 @@ __device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long lon
   if constexpr (ROLE == P_HMID) {
     const C* __restrict__ f = static_cast<const C*>((a.f && !a.solver) ? a.f : a.phi);
     const C* tb = static_cast<const C*>(a.t);
+    C tv[E];  // the accumulated t, loaded before the transforms so the loads overlap them
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = f[base + (t + q * Tl) * st];
+    for (int q = 0; q < E; ++q) {
+      v[q] = f[base + (t + q * Tl) * st];
+      tv[q] = tb[base + (t + q * Tl) * st];
+    }
     line_dft<M, E, -1>(v, sm, si, t, tw);
     const T om = T(a.omega);
     const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
@@ -650,10 +654,7 @@ __device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long lon
     line_dft<M, E, +1>(v, sm, si, t, tw);
     C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: final pass writes the caller's buffer
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const long long g = base + (t + q * Tl) * st;
-      dst[g] = cadd(tb[g], v[q]);
-    }
+    for (int q = 0; q < E; ++q) dst[base + (t + q * Tl) * st] = cadd(tv[q], v[q]);
     acc[0] = acc_add(acc[0], acc_from(akin * invM));
     acc[1] = acc_add(acc[1], acc_from(arot * invM));
   } else if constexpr (ROLE == P_CFWD || ROLE == P_CINV || ROLE == P_CCORE) {
