@@ -202,6 +202,26 @@ def precond_C(prob, phi, r, alpha):
     return s * precond_delta(prob, s * r, alpha)
 
 
+def apply_preconditioner(prob, phi, r, alpha, kind):
+    """P r for the preconditioners of Section 5.4, all with the shift alpha:
+    "C" P_V^{1/2} P_Delta P_V^{1/2} (eq. combinedP_12), "Delta" P_Delta (eq. PDelta),
+    "V" P_V (eq. PV), "C1" P_V P_Delta and "C2" P_Delta P_V (eq. combinedP; the
+    right factor acts first), "none" the identity."""
+    if kind == "C":
+        return precond_C(prob, phi, r, alpha)
+    if kind == "Delta":
+        return precond_delta(prob, r, alpha)
+    if kind == "V":
+        return precond_V(prob, phi, alpha) * r
+    if kind == "C1":
+        return precond_V(prob, phi, alpha) * precond_delta(prob, r, alpha)
+    if kind == "C2":
+        return precond_delta(prob, precond_V(prob, phi, alpha) * r, alpha)
+    if kind == "none":
+        return r.copy()
+    raise ValueError(kind)
+
+
 # --------------------------------------------------------------------------
 # Line search along the geodesic (Section 5.1, readings R4-R6)
 # --------------------------------------------------------------------------
@@ -264,7 +284,8 @@ class SolveOptions:
     max_iter: int = 20000
     theta_default: float = 0.1     # trial step when the model curvature is <= 0 (R5)
     max_backtracks: int = 30       # theta <- theta/2 at most this many times (R5)
-    precond: str = "C"             # "C" (symmetric combined) or "none"
+    precond: str = "C"             # "C", "Delta", "V", "C1", "C2" or "none" (apply_preconditioner)
+    beta: str = "PR"               # "PR": max(beta_PR, 0) (eq. CG:PR); "FR": Fletcher-Reeves (eq. CG:FR)
     cg: bool = True                # False: the projected gradient method (Algorithm 1)
 
 
@@ -300,13 +321,12 @@ def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterat
             break
 
         alpha = lambda_tilde(prob, phi)                    # eq. Opt_Alpha
-        if opts.precond == "C":
-            Pr = precond_C(prob, phi, r, alpha)
-        else:
-            Pr = r.copy()
+        Pr = apply_preconditioner(prob, phi, r, alpha, opts.precond)
         rPr = inner(prob, r, Pr).real
         if not opts.cg or n == 0 or rPr_prev is None:
             beta = 0.0
+        elif opts.beta == "FR":
+            beta = rPr / rPr_prev                                 # eq. CG:FR
         else:
             beta = max(inner(prob, r - r_prev, Pr).real / rPr_prev, 0.0)  # eq. CG:PR, beta+
         d = -Pr + beta * p_prev if beta != 0.0 else -Pr

@@ -28,6 +28,7 @@ QUICK_PINS = [
     lambda: P.test_P11_hellmann_feynman_matches_differences_of_solves(P.solve_ground_state_16()),
     lambda: P.test_P12_hessian_operator_is_the_second_order_form(P.solve_ground_state_16()),
     lambda: P.test_P12_density_loss_gradient_matches_differences_of_solves(P.solve_ground_state_16()),
+    P.test_P6_preconditioner_variants_adjointness,
 ]
 
 
@@ -134,6 +135,19 @@ def _dloss_wrong_sign(prob, phi, rho, tol=1e-12, max_iter=5000):
     return -g, it, res
 
 
+_orig_apply_pc = O.apply_preconditioner
+
+
+def _c2_as_c1(prob, phi, r, alpha, kind):
+    return _orig_apply_pc(prob, phi, r, alpha, "C1" if kind == "C2" else kind)
+
+
+def _pv_sqrt(prob, phi, r, alpha, kind):
+    if kind == "V":
+        return np.sqrt(O.precond_V(prob, phi, alpha)) * r
+    return _orig_apply_pc(prob, phi, r, alpha, kind)
+
+
 MUTATIONS = {
     "Lz_sign": ("Lz", _lz_wrong_sign),
     "Lz_axes": ("Lz", _lz_swapped_axes),
@@ -149,6 +163,8 @@ MUTATIONS = {
     "deta_no_half": ("energy_parameter_derivatives", _deta_without_half),
     "hessian_no_conj": ("hessian_apply", _hessian_without_conjugate_term),
     "dloss_sign": ("density_loss_gradient_V", _dloss_wrong_sign),
+    "pc_c2_as_c1": ("apply_preconditioner", _c2_as_c1),
+    "pc_v_sqrt": ("apply_preconditioner", _pv_sqrt),
 }
 
 

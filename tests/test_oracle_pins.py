@@ -364,3 +364,56 @@ def test_P12_density_loss_gradient_matches_differences_of_solves(ground_state_16
         fd = (O.density_loss(p, fp, rho) - O.density_loss(p, fm, rho)) / (2 * h)
         an = np.sum(gV * S)
         assert abs(fd - an) < 1e-5 * abs(an)
+
+
+# ---------------------------------------------------------------- P6b / P8b: preconditioner variants
+def test_P6_preconditioner_variants_adjointness():
+    """P_V and P_Delta are self-adjoint, so P_C, P_Delta, P_V are self-adjoint and
+    P_C1 = P_V P_Delta and P_C2 = P_Delta P_V (eq. combinedP) are each other's
+    adjoints, <f, P_C1 g> = <P_C2 f, g>, while P_C1 itself is not self-adjoint."""
+    p = prob2(M=16, eta=5.0)
+    n, L = p.n, p.L
+    phi = I.normalise(I.phi_d(n, L, 0.4) * (1 + 0.3 * I.random_field(41, n, L)), n, L)
+    f, g = I.random_field(42, n, L), I.random_field(43, n, L)
+    a = 2.3
+
+    def P(x, kind):
+        return O.apply_preconditioner(p, phi, x, a, kind)
+
+    for kind in ("C", "Delta", "V", "none"):
+        lhs, rhs = O.inner(p, f, P(g, kind)), O.inner(p, P(f, kind), g)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs), kind
+    lhs, rhs = O.inner(p, f, P(g, "C1")), O.inner(p, P(f, "C2"), g)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    asym = O.inner(p, f, P(g, "C1")) - O.inner(p, P(f, "C1"), g)
+    assert abs(asym) > 1e-3 * abs(lhs)
+    # P_V is the inverse of multiplication by alpha + V + eta |phi|^2
+    m = a + p.V + p.eta * np.abs(phi) ** 2
+    assert np.max(np.abs(m * P(g, "V") - g)) < 1e-13 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("precond,beta", [("C", "PR"), ("Delta", "PR"), ("V", "PR"), ("C1", "PR"),
+                                          ("C2", "PR"), ("none", "PR"), ("C", "FR")])
+def test_P8_every_preconditioner_reaches_the_same_ground_state(precond, beta):
+    """The ground state does not depend on the preconditioner or on the
+    conjugation rule: each variant converges (||r||_inf < 1e-9) to the energy of
+    the default (P_C, Polak-Ribiere) solve, with monotone energy decrease."""
+    n, L = (64, 64), (8.0, 8.0)
+    p = O.Problem(n, L, 100.0, 0.2, I.harmonic(n, L))
+    phi0 = I.perturbed(I.phi_a(n, L), 7, n, L)
+    ref = _P8_reference(p, phi0)
+    _, rep = O.pcg_solve(p, phi0, O.SolveOptions(tol_res_inf=1e-9, max_iter=5000, precond=precond, beta=beta))
+    assert rep["status"] == "converged", (precond, beta, rep["iters"])
+    assert abs(rep["E"] - ref) < 1e-11 * abs(ref)
+    Es = [e["E"] for e in rep["log"]]
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(Es, Es[1:]))
+
+
+_P8_REF = {}
+
+
+def _P8_reference(p, phi0):
+    if "E" not in _P8_REF:
+        _, rep = O.pcg_solve(p, phi0, O.SolveOptions(tol_res_inf=1e-10))
+        _P8_REF["E"] = rep["E"]
+    return _P8_REF["E"]
