@@ -95,7 +95,23 @@ typedef struct {
   int refine_restart;   /* GPE_MIXED: 1 restarts the conjugate directions (beta = 0, p = 0) when the
                          * complex128 phase starts; 0 carries the last complex64 direction p_{n-1},
                          * r_{n-1} and <r_{n-1}, P r_{n-1}> over [1] */
+  int precond;          /* [GPE_PRECOND_C] preconditioner of Section 5.4 (below) */
+  int beta_rule;        /* [GPE_BETA_PR] conjugation coefficient (below) */
 } gpe_solve_opts;
+
+/* gpe_solve_opts.precond, with alpha = lambda~_n (eq. Opt_Alpha) in every case:
+ *  GPE_PRECOND_C     P_V^{1/2} P_Delta P_V^{1/2}            (eq. combinedP_12)
+ *  GPE_PRECOND_DELTA P_Delta = (alpha - Delta/2)^{-1}          (eq. PDelta)
+ *  GPE_PRECOND_V     P_V = (alpha + V + eta|phi_n|^2)^{-1}     (eq. PV)
+ *  GPE_PRECOND_C1    P_V P_Delta                              (eq. combinedP)
+ *  GPE_PRECOND_C2    P_Delta P_V                              (eq. combinedP)
+ *  GPE_PRECOND_NONE  identity
+ * gpe_solve_opts.beta_rule:
+ *  GPE_BETA_PR  max(beta_PR, 0) with beta_PR = Re<r_n - r_{n-1}, P r_n> / <r_{n-1}, P r_{n-1}> (eq. CG:PR)
+ *  GPE_BETA_FR  <r_n, P r_n> / <r_{n-1}, P r_{n-1}> (eq. CG:FR) */
+enum { GPE_PRECOND_C = 0, GPE_PRECOND_DELTA = 1, GPE_PRECOND_V = 2, GPE_PRECOND_C1 = 3, GPE_PRECOND_C2 = 4,
+       GPE_PRECOND_NONE = 5 };
+enum { GPE_BETA_PR = 0, GPE_BETA_FR = 1 };
 
 /* Per-iteration log row, doubles: */
 #define GPE_LOG_FIELDS 12

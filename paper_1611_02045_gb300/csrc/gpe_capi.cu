@@ -285,6 +285,8 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->max_iter_lo = 0;
   o->use_graph = 3;
   o->refine_restart = 1;
+  o->precond = GPE_PRECOND_C;
+  o->beta_rule = GPE_BETA_PR;
   return GPE_OK;
 }
 
@@ -865,6 +867,7 @@ static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
   h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
   h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
   h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
+  h.pc_kind = o.precond; h.beta_rule = o.beta_rule;
   double k2 = 0.0;  // max over the grid of |k|^2 / 2 (corner mode -M/2 on every axis)
   for (int i = 0; i < c->dim; ++i) {
     const double km = 0.5 * c->n[i] * M_PI / c->prob.L[i];
@@ -876,7 +879,8 @@ static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
 }
 
 static gpe_status check_opts(gpe_solve_opts& o, std::string& err) {
-  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1) {
+  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1 || o.precond < 0 ||
+      o.precond > 5 || o.beta_rule < 0 || o.beta_rule > 1) {
     err = "invalid solve options";
     return GPE_ERR_ARG;
   }

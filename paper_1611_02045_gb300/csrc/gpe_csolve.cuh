@@ -87,10 +87,11 @@ __device__ __forceinline__ void cs_yunit(const cgc::cluster_group& cl, int rank,
     const float alpha = float(S.alpha);
     const float invN = 1.0f / float(M * M);
     const float kx = static_cast<const float*>(a.xi[0])[x];
+    const bool core = pc_core(S.pc);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const float k = xiy[t + q * Tl];
-      w[q] = cscale(w[q], invN / (alpha + 0.5f * (kx * kx + k * k)));
+      w[q] = cscale(w[q], core ? invN / (alpha + 0.5f * (kx * kx + k * k)) : invN);
     }
     line_dft<M, E, +1>(w, xs, si, t, tw);
 #pragma unroll

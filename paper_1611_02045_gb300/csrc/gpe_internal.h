@@ -19,6 +19,9 @@ struct Ctl {
   double tol_res_inf, tol_dE, theta_default, switch_res;
   int max_iter, max_backtracks, cg, stall_window, max_iter_phase, phase;
   int lo_phase;  // 1 while running the complex64 phase of a mixed solve
+  int pc_kind;   // preconditioner: 0 P_C (symmetric combined), 1 P_Delta, 2 P_V, 3 P_C1 = P_V P_Delta,
+                 // 4 P_C2 = P_Delta P_V, 5 none
+  int beta_rule; // 0 Polak-Ribiere beta+ (eq. CG:PR), 1 Fletcher-Reeves (eq. CG:FR)
   // ---- loop state ----
   int iter;        // n (global over both phases)
   int iter_phase0; // value of iter when this phase started

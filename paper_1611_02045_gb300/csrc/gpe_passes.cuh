@@ -263,7 +263,9 @@ static __device__ void finalize_C3(Ctl* c, const Fin& a, const double (&tot)[6],
   const double w = a.weight;
   const double rPr = w * tot[0];
   double beta = 0.0;
-  if (!c->restart && c->cg) beta = fmax(w * tot[1] / c->rPr_prev, 0.0);
+  if (!c->restart && c->cg)
+    beta = c->beta_rule == 1 ? rPr / c->rPr_prev                  // Fletcher-Reeves (eq. CG:FR)
+                             : fmax(w * tot[1] / c->rPr_prev, 0.0);  // Polak-Ribiere beta+
   const double Prphi = w * tot[2], pphi = w * tot[3], rp = w * tot[4], rphi = w * tot[5];
   double gamma = -Prphi + beta * pphi;
   // Re<H phi, p> = Re<r, d> - gamma Re<r, phi> + lambda gamma (1 - ||phi||^2)
@@ -350,12 +352,30 @@ __device__ __forceinline__ void set_loop_condition(const PassArgs& a, int keep_g
 // Scalars a pass body reads (copied from the control block at entry).
 struct Scal {
   int retract;
+  int pc;  // preconditioner kind (Ctl::pc_kind; API calls: 0, P_C)
   double c, s, inv_np, inv_nrm, lam, alpha, beta, gamma;
 };
+
+// The preconditioners of Section 5.4 as P_V^a P_Delta^b P_V^c around the
+// Fourier core: exponents of P_V before (pre) and after (post) the core,
+// coded 0 (none), 1 (P_V^{1/2}), 2 (P_V), and whether the core divides by
+// alpha + |k|^2/2 (P_Delta, eq. PDelta) or is the identity.
+//   P_C  = P_V^{1/2} P_Delta P_V^{1/2} (eq. combinedP_12): 1, Delta, 1
+//   P_Delta (eq. PDelta): 0, Delta, 0      P_V (eq. PV): 2, identity, 0
+//   P_C1 = P_V P_Delta (eq. combinedP): 0, Delta, 2  (P_Delta first)
+//   P_C2 = P_Delta P_V (eq. combinedP): 2, Delta, 0  (P_V first)
+//   none: 0, identity, 0
+__device__ __forceinline__ int pc_pre(int k) { return k == 0 ? 1 : (k == 2 || k == 4) ? 2 : 0; }
+__device__ __forceinline__ int pc_post(int k) { return k == 0 ? 1 : k == 3 ? 2 : 0; }
+__device__ __forceinline__ bool pc_core(int k) { return !(k == 2 || k == 5); }
+template <typename T> __device__ __forceinline__ T pv_factor(T den, int code) {
+  return code == 0 ? T(1) : (code == 2 ? T(1) / den : T(1) / sqrt(den));
+}
 
 __device__ __forceinline__ Scal scal_of(const Ctl* c, const PassArgs& a) {
   Scal S;
   S.retract = a.solver ? c->retract : 0;
+  S.pc = a.solver ? c->pc_kind : 0;
   S.c = c->c; S.s = c->s; S.inv_np = c->inv_np; S.inv_nrm = c->inv_nrm;
   S.lam = a.solver ? c->lam : 0.0;
   S.alpha = a.solver ? c->alpha : (a.api_alpha > 0 ? a.api_alpha : c->alpha);
@@ -484,6 +504,8 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     const TS alpha = TS(S.alpha);
     const TS eta = TS(a.eta);
     TS rmax = 0, r2 = 0, bad = 0;
+    const int pre = pc_pre(S.pc);
+    const bool uses_pv = pre != 0 || pc_post(S.pc) != 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
@@ -491,10 +513,10 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
       CS r = rin[g];
       if (a.solver) r = cmk<CS>(r.x - lam * ph.x, r.y - lam * ph.y);
       const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
-      bad += (den > TS(0)) ? TS(0) : TS(1);
+      bad += (den > TS(0) || !uses_pv) ? TS(0) : TS(1);
       const TS a2 = r.x * r.x + r.y * r.y;
       rmax = fmax(rmax, a2); r2 += a2;
-      v[q] = cconv<TF>(cscale(r, TS(1) / sqrt(den)));
+      v[q] = cconv<TF>(cscale(r, pv_factor(den, pre)));
     }
     line_dft<M, E, -1, W>(v, sm, si, t, tw);
     CD* __restrict__ sout = static_cast<CD*>(a.s);
@@ -519,7 +541,7 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
         const long long g = base + t + q * Tl;
         const CS ph = phi[g];
         const TS den = alpha + V[g] + eta * (ph.x * ph.x + ph.y * ph.y);
-        out[g] = cconv<TD>(cscale(cconv<TS>(v[q]), TS(1) / sqrt(den)));
+        out[g] = cconv<TD>(cscale(cconv<TS>(v[q]), pv_factor(den, pc_post(S.pc))));
       }
       return;
     }
@@ -542,12 +564,13 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     }
     line_dft<M, E, +1, W>(v, sm, si, t, tw);
     const TS lam = TS(S.lam);
+    const int post = pc_post(S.pc);
     TS a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const long long g = base + t + q * Tl;
       const TS den = alpha + vv[q] + eta * (ph[q].x * ph[q].x + ph[q].y * ph[q].y);
-      const CD Prd = cconv<TD>(cscale(cconv<TS>(v[q]), TS(1) / sqrt(den)));
+      const CD Prd = cconv<TD>(cscale(cconv<TS>(v[q]), pv_factor(den, post)));
       sbuf[g] = Prd;
       const CS Pr = cconv<TS>(Prd);  // the stored direction, as later passes see it
       const CS r = cmk<CS>(hq[q].x - lam * ph[q].x, hq[q].y - lam * ph[q].y);
@@ -678,10 +701,12 @@ __device__ __forceinline__ void sunit(const PassArgs& a, const Scal& S, long lon
         kother = ky * ky;
       }
 #pragma unroll
+      const bool core = pc_core(S.pc);
+#pragma unroll
       for (int q = 0; q < E; ++q) {
         const T k = xia[t + q * Tl];
         const T den = alpha + T(0.5) * (kx * kx + kother + k * k);
-        v[q] = cscale(v[q], invN / den);
+        v[q] = cscale(v[q], core ? invN / den : invN);
       }
       line_dft<M, E, +1>(v, sm, si, t, tw);
     }

@@ -19,6 +19,8 @@ _LIB_PATH = Path(__file__).resolve().parent / "libgpe.so"
 GPE_OK, GPE_ERR_ARG, GPE_ERR_CUDA, GPE_ERR_NOT_CONVERGED, GPE_ERR_NONFINITE, GPE_ERR_PRECOND, \
     GPE_ERR_TIMEOUT, GPE_ERR_UNSUPPORTED = range(8)
 GPE_FP64, GPE_MIXED = 0, 1
+GPE_PRECOND_C, GPE_PRECOND_DELTA, GPE_PRECOND_V, GPE_PRECOND_C1, GPE_PRECOND_C2, GPE_PRECOND_NONE = range(6)
+GPE_BETA_PR, GPE_BETA_FR = 0, 1
 GPE_LOG_FIELDS = 12
 LOG_COLUMNS = ("n", "phase", "E", "lam", "res_inf", "res_l2", "alpha", "beta", "theta", "dE",
                "fallback", "backtracks")
@@ -35,7 +37,8 @@ class gpe_solve_opts(C.Structure):
     _fields_ = [("tol_res_inf", C.c_double), ("tol_dE", C.c_double), ("max_iter", C.c_int),
                 ("theta_default", C.c_double), ("max_backtracks", C.c_int), ("cg", C.c_int),
                 ("stall_window", C.c_int), ("switch_res", C.c_double), ("max_iter_lo", C.c_int),
-                ("use_graph", C.c_int), ("refine_restart", C.c_int)]
+                ("use_graph", C.c_int), ("refine_restart", C.c_int), ("precond", C.c_int),
+                ("beta_rule", C.c_int)]
 
 
 class gpe_report(C.Structure):
