@@ -266,6 +266,44 @@ def delta_energy(m, eta, theta):
                            + 4.0 * c * s ** 3 * (m["VW"] - m["U1"])))
 
 
+def delta_energy_derivatives(m, eta, theta):
+    """First and second derivatives in t of delta_energy (same moments): with
+    c = cos t, s = sin t, A = aqq - lam, B = eta/2 (U0 + W2), C = eta/2 (4 V2 + 2 UW),
+    D = 2 eta (VW - U1), delta_energy = 2cs R + s^2 A + s^4 B + c^2 s^2 C + c s^3 D and
+        d/dt   = 2R cos 2t + A sin 2t + 4B s^3 c + C/2 sin 4t + D (3 c^2 s^2 - s^4),
+        d2/dt2 = -4R sin 2t + 2A cos 2t + 4B (3 s^2 c^2 - s^4) + 2C cos 4t + D (6 c s (c^2 - s^2) - 4 s^3 c)."""
+    c, s = np.cos(theta), np.sin(theta)
+    A = m["aqq"] - m["lam"]
+    B = 0.5 * eta * (m["U0"] + m["W2"])
+    C = 0.5 * eta * (4.0 * m["V2"] + 2.0 * m["UW"])
+    D = 2.0 * eta * (m["VW"] - m["U1"])
+    R = m["R"]
+    d1 = (2.0 * R * np.cos(2 * theta) + A * np.sin(2 * theta) + 4.0 * B * s ** 3 * c + 0.5 * C * np.sin(4 * theta)
+          + D * (3.0 * c * c * s * s - s ** 4))
+    d2 = (-4.0 * R * np.sin(2 * theta) + 2.0 * A * np.cos(2 * theta) + 4.0 * B * (3.0 * s * s * c * c - s ** 4)
+          + 2.0 * C * np.cos(4 * theta) + D * (6.0 * c * s * (c * c - s * s) - 4.0 * s ** 3 * c))
+    return d1, d2
+
+
+def exact_step(m, eta, theta0, iters=30):
+    """The step minimising delta_energy near theta0 ("full line search" variant):
+    Newton's method on d/dt delta_energy = 0 from theta0, stopping when the
+    update is below 1e-15 |t|; returns theta0 when the curvature is not positive
+    or the iteration leaves (0, pi/2]."""
+    t = theta0
+    for _ in range(iters):
+        d1, d2 = delta_energy_derivatives(m, eta, t)
+        if not d2 > 0.0:
+            return theta0
+        dt = d1 / d2
+        t = t - dt
+        if not (0.0 < t <= 0.5 * np.pi):
+            return theta0
+        if abs(dt) <= 1e-15 * abs(t):
+            break
+    return t
+
+
 def model_curvature(prob, phi, lam, q):
     """T2(q) - lambda: the theta^2 coefficient of the energy along the geodesic
     (eq. expansion_energy read as E + 2t Re<r,q> + t^2 (T2(q) - lambda), R4)."""
@@ -286,6 +324,7 @@ class SolveOptions:
     max_backtracks: int = 30       # theta <- theta/2 at most this many times (R5)
     precond: str = "C"             # "C", "Delta", "V", "C1", "C2" or "none" (apply_preconditioner)
     beta: str = "PR"               # "PR": max(beta_PR, 0) (eq. CG:PR); "FR": Fletcher-Reeves (eq. CG:FR)
+    line_search: str = "model"     # "model": theta_0 of R4 + backtracking; "exact": Newton from theta_0
     cg: bool = True                # False: the projected gradient method (Algorithm 1)
 
 
@@ -342,6 +381,8 @@ def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterat
         m = step_moments(prob, phi, Hphi, lam, q)
         curv = model_curvature(prob, phi, lam, q)
         theta = -m["R"] / curv if curv > 0.0 else opts.theta_default  # eq. theta_opt
+        if opts.line_search == "exact":
+            theta = exact_step(m, prob.eta, theta)
         dE = delta_energy(m, prob.eta, theta)
         backtracks = 0
         while not dE < 0.0 and backtracks < opts.max_backtracks:
@@ -366,6 +407,32 @@ def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterat
             break
     return phi, dict(status=status, iters=n, log=log, iterates=iterates,
                      E=log[-1]["E"], lam=log[-1]["lam"], res_inf=log[-1]["res_inf"])
+
+
+# --------------------------------------------------------------------------
+# Thomas-Fermi initial data (Section 6, eq. TF_App)
+# --------------------------------------------------------------------------
+
+
+def thomas_fermi_mu(prob, iters=200):
+    """mu with h^d sum max(mu - V, 0) / eta = 1, i.e. ||phi^TF|| = 1 for
+    phi^TF = sqrt(max(mu - V, 0) / eta): bisection on [min V, max V + eta / (h^d N)]."""
+    V, w, eta = prob.V, prob.weight, prob.eta
+    lo, hi = float(V.min()), float(V.max()) + eta / (w * V.size)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if w * np.sum(np.maximum(mid - V, 0.0)) / eta < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def thomas_fermi_state(prob):
+    """phi_0 = phi^TF / ||phi^TF|| of eq. TF_App (with the mu above, ||phi^TF|| = 1)."""
+    mu = thomas_fermi_mu(prob)
+    phi = np.sqrt(np.maximum(mu - prob.V, 0.0) / prob.eta) + 0j
+    return phi / norm(prob, phi), mu
 
 
 # --------------------------------------------------------------------------

@@ -29,6 +29,8 @@ QUICK_PINS = [
     lambda: P.test_P12_hessian_operator_is_the_second_order_form(P.solve_ground_state_16()),
     lambda: P.test_P12_density_loss_gradient_matches_differences_of_solves(P.solve_ground_state_16()),
     P.test_P6_preconditioner_variants_adjointness,
+    P.test_P5_line_search_derivatives_match_differences,
+    P.test_P5_exact_step_minimises_the_energy_along_the_geodesic,
 ]
 
 
@@ -148,6 +150,16 @@ def _pv_sqrt(prob, phi, r, alpha, kind):
     return _orig_apply_pc(prob, phi, r, alpha, kind)
 
 
+_orig_dderiv = O.delta_energy_derivatives
+
+
+def _dderiv_wrong_quartic(m, eta, theta):
+    d1, d2 = _orig_dderiv(m, eta, theta)
+    c, s_ = np.cos(theta), np.sin(theta)
+    B = 0.5 * eta * (m["U0"] + m["W2"])
+    return d1 - 2.0 * B * s_ ** 3 * c, d2
+
+
 MUTATIONS = {
     "Lz_sign": ("Lz", _lz_wrong_sign),
     "Lz_axes": ("Lz", _lz_swapped_axes),
@@ -165,6 +177,7 @@ MUTATIONS = {
     "dloss_sign": ("density_loss_gradient_V", _dloss_wrong_sign),
     "pc_c2_as_c1": ("apply_preconditioner", _c2_as_c1),
     "pc_v_sqrt": ("apply_preconditioner", _pv_sqrt),
+    "line_deriv_quartic": ("delta_energy_derivatives", _dderiv_wrong_quartic),
 }
 
 

@@ -417,3 +417,80 @@ def _P8_reference(p, phi0):
         _, rep = O.pcg_solve(p, phi0, O.SolveOptions(tol_res_inf=1e-10))
         _P8_REF["E"] = rep["E"]
     return _P8_REF["E"]
+
+
+# ---------------------------------------------------------------- P5b: exact line search
+def _line_moments(seed=51):
+    p = _grad_problem()
+    n, L = p.n, p.L
+    phi = I.normalise(I.phi_d(n, L, 0.5) * (1 + 0.2 * I.random_field(seed, n, L)), n, L)
+    lam = O.chemical_potential(p, phi)
+    Hphi = O.apply_H(p, phi, phi)
+    r = Hphi - lam * phi
+    q = -O.precond_C(p, phi, r, O.lambda_tilde(p, phi))
+    q = q - O.inner(p, q, phi).real * phi
+    q = q / O.norm(p, q)
+    return p, O.step_moments(p, phi, Hphi, lam, q)
+
+
+def test_P5_line_search_derivatives_match_differences():
+    """The closed-form first and second derivatives of the step polynomial
+    against central differences of delta_energy at several steps."""
+    p, m = _line_moments()
+    h = 1e-5
+    for t in (0.01, 0.1, 0.4, 1.0):
+        d1, d2 = O.delta_energy_derivatives(m, p.eta, t)
+        f = lambda x: O.delta_energy(m, p.eta, x)  # noqa: E731
+        fd1 = (f(t + h) - f(t - h)) / (2 * h)
+        fd2 = (O.delta_energy_derivatives(m, p.eta, t + h)[0] - O.delta_energy_derivatives(m, p.eta, t - h)[0]) / (2 * h)
+        assert abs(d1 - fd1) < 1e-7 * max(abs(d1), 1e-3), t
+        assert abs(d2 - fd2) < 1e-6 * max(abs(d2), 1e-3), t
+
+
+def test_P5_exact_step_minimises_the_energy_along_the_geodesic():
+    """The Newton step is the minimiser of the energy along cos t phi + sin t q
+    near the model step: no point of a dense scan of the direct energy
+    difference is lower, and the derivative vanishes there."""
+    p, m = _line_moments()
+    curv = m["aqq"] - m["lam"]
+    t0 = -m["R"] / curv
+    ts = O.exact_step(m, p.eta, t0)
+    assert ts != t0 and 0 < ts < 1.5
+    assert abs(O.delta_energy_derivatives(m, p.eta, ts)[0]) < 1e-12 * max(abs(m["R"]), 1e-12)
+    grid = np.linspace(0.5 * ts, 1.5 * ts, 2001)
+    vals = np.array([O.delta_energy(m, p.eta, t) for t in grid])
+    assert O.delta_energy(m, p.eta, ts) <= vals.min() + 1e-14 * abs(vals.min())
+    assert O.delta_energy(m, p.eta, ts) <= O.delta_energy(m, p.eta, t0)
+
+
+# ---------------------------------------------------------------- P13: Thomas-Fermi initial data
+@pytest.mark.parametrize("gammas", [(1.0, 1.0), (1.0, 1.5)])
+def test_P13_thomas_fermi_mu_matches_the_continuum_closed_form_2d(gammas):
+    """For V = sum gamma_i^2 x_i^2 / 2 the region V < mu is an ellipse and
+    int max(mu - V, 0) / eta = pi mu^2 / (eta gamma_x gamma_y) = 1 gives
+    mu = sqrt(eta gamma_x gamma_y / pi); the grid sum converges to it."""
+    n, L = (512, 512), (16.0, 16.0)
+    eta = 1000.0
+    p = O.Problem(n, L, eta, 0.0, I.harmonic(n, L, list(gammas)))
+    mu = O.thomas_fermi_mu(p)
+    want = np.sqrt(eta * gammas[0] * gammas[1] / np.pi)
+    assert abs(mu - want) < 2e-4 * want
+    phi, mu2 = O.thomas_fermi_state(p)
+    assert mu2 == mu and abs(O.norm(p, phi) - 1.0) < 1e-14
+    # the unnormalised state already has unit norm (the defining condition)
+    raw = np.sqrt(np.maximum(mu - p.V, 0.0) / eta)
+    assert abs(p.weight * np.sum(raw ** 2) - 1.0) < 1e-12
+
+
+def test_P13_thomas_fermi_mu_matches_the_continuum_closed_form_3d():
+    """3D: with y_i = g_i x_i / sqrt(2 mu) the region is the unit ball and
+    int max(mu - V, 0) = (2 mu)^{3/2} mu (4 pi/3 - 4 pi/5) / (g_x g_y g_z)
+    = 16 sqrt(2) pi mu^{5/2} / (15 g_x g_y g_z), so
+    mu = (15 eta g_x g_y g_z / (16 sqrt(2) pi))^{2/5}."""
+    n, L = (128, 128, 128), (8.0, 8.0, 8.0)
+    g = (1.0, 1.0, 2.0)
+    eta = 5000.0
+    p = O.Problem(n, L, eta, 0.0, I.harmonic(n, L, list(g)))
+    mu = O.thomas_fermi_mu(p)
+    want = (15.0 * eta * g[0] * g[1] * g[2] / (16.0 * np.sqrt(2.0) * np.pi)) ** 0.4
+    assert abs(mu - want) < 2e-3 * want
