@@ -97,6 +97,7 @@ typedef struct {
                          * r_{n-1} and <r_{n-1}, P r_{n-1}> over [1] */
   int precond;          /* [GPE_PRECOND_C] preconditioner of Section 5.4 (below) */
   int beta_rule;        /* [GPE_BETA_PR] conjugation coefficient (below) */
+  int line_search;      /* [GPE_LINE_MODEL] step size (below) */
 } gpe_solve_opts;
 
 /* gpe_solve_opts.precond, with alpha = lambda~_n (eq. Opt_Alpha) in every case:
@@ -112,6 +113,14 @@ typedef struct {
 enum { GPE_PRECOND_C = 0, GPE_PRECOND_DELTA = 1, GPE_PRECOND_V = 2, GPE_PRECOND_C1 = 3, GPE_PRECOND_C2 = 4,
        GPE_PRECOND_NONE = 5 };
 enum { GPE_BETA_PR = 0, GPE_BETA_FR = 1 };
+/* gpe_solve_opts.line_search (Section 5.1; the energy-decrease backtracking
+ * applies after either):
+ *  GPE_LINE_MODEL  theta_0 = -Re<H phi, q> / (T2(q) - lambda), the minimiser of
+ *                  the second-order model (theta_default when the curvature is <= 0)
+ *  GPE_LINE_EXACT  Newton's method from theta_0 on d/dtheta of the exact energy
+ *                  change E(cos t phi + sin t q) - E(phi), a trigonometric
+ *                  polynomial in t fixed by the step moments (full line search) */
+enum { GPE_LINE_MODEL = 0, GPE_LINE_EXACT = 1 };
 
 /* Per-iteration log row, doubles: */
 #define GPE_LOG_FIELDS 12
@@ -258,6 +267,16 @@ gpe_status gpe_tangent_solve(gpe_ctx* ctx, const void* phi_dev, const void* rhs_
  * computed from the last iterate. */
 gpe_status gpe_density_adjoint(gpe_ctx* ctx, const void* phi_dev, const double* g_rho_dev, double* grad_V_dev,
                                double tol, int max_iter, int* iters, double* rel_res);
+
+/* Thomas-Fermi initial data (Section 6, eq. TF_App): phi_0 = sqrt(max(mu - V, 0) / eta),
+ * with mu fixed by the normalisation h^d sum max(mu - V, 0) / eta = 1 (so that
+ * ||phi_0|| = 1), found by bisection on the device (120 halvings of the bracket
+ * [min V, max V + eta / (h^d N)]).  The closed forms of eq. TF_Rdius hold for
+ * the paper's harmonic traps only; the normalisation holds for any V.
+ *  phi_out : complex128 [z][y][x], host or device.
+ *  mu_out  : may be NULL; receives mu.
+ * Synchronises the stream.  Errors: GPE_ERR_ARG (eta <= 0), GPE_ERR_CUDA. */
+gpe_status gpe_thomas_fermi(gpe_ctx* ctx, void* phi_out, double* mu_out);
 
 /* Ground state by Algorithm 2 (PCG) with the symmetric combined
  * preconditioner P_C, the Polak-Ribiere coefficient beta = max(beta_PR, 0)

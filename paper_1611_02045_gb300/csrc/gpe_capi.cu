@@ -73,6 +73,8 @@ struct gpe_ctx {
   int hbatch_E = 8;      // values per thread of gpe_apply_H_batch's cluster kernel (plan mode 3):
                          // 16 (streaming form) by default in single precision for n >= 64
   double vmax = 0.0;  // max V on the grid
+  double vmin = 0.0;  // min V on the grid
+  double* tf_state = nullptr;  // Thomas-Fermi bisection bracket (2 doubles, device)
   int max_threads[2] = {512, 256};
   bool warmed[3] = {false, false, false};  // per launch mode
   int nsm = 0;                      // streaming multiprocessors of the device
@@ -229,12 +231,14 @@ static gpe_status load_V(gpe_ctx* c, const double* V, double** V64_out) {
       cudaMemcpy(Vh.data(), V64, 8 * (size_t)c->N, cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaFree(V64); c->err = "copy of V failed"; return GPE_ERR_CUDA;
   }
-  double vm = -1e300;
+  double vm = -1e300, vn = 1e300;
   for (double v : Vh) {
     if (!std::isfinite(v)) { cudaFree(V64); c->err = "V must be finite"; return GPE_ERR_ARG; }
     vm = v > vm ? v : vm;
+    vn = v < vn ? v : vn;
   }
   c->vmax = vm;
+  c->vmin = vn;
   *V64_out = V64;
   return GPE_OK;
 }
@@ -266,6 +270,7 @@ static void free_ctx(gpe_ctx* c) {
   }
   cudaFree(c->pers_partials); cudaFree(c->pers_bar);
   for (auto& a : c->adj) cudaFree(a);
+  cudaFree(c->tf_state);
   cudaFree(c->adj_s); cudaFree(c->adj_partials);
   cudaFree(c->ctl_solve); cudaFree(c->ctl_api); cudaFree(c->partials); cudaFree(c->ticket); cudaFree(c->log_dev);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -287,6 +292,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->refine_restart = 1;
   o->precond = GPE_PRECOND_C;
   o->beta_rule = GPE_BETA_PR;
+  o->line_search = GPE_LINE_MODEL;
   return GPE_OK;
 }
 
@@ -475,6 +481,28 @@ extern "C" gpe_status gpe_energy_grad(gpe_ctx* c, const void* phi, void* grad_ph
 // in gpe_adjoint.cu).  Declared below run_PC.
 static gpe_status tangent_solve(gpe_ctx* c, const void* phi, const void* rhs, void* z, double tol, int max_iter,
                                 int* iters, double* rel_res);
+
+extern "C" gpe_status gpe_thomas_fermi(gpe_ctx* c, void* phi_out, double* mu_out) {
+  if (!c) return GPE_ERR_ARG;
+  if (!phi_out) { c->err = "null phi"; return GPE_ERR_ARG; }
+  if (!(c->prob.eta > 0.0)) { c->err = "the Thomas-Fermi state needs eta > 0"; return GPE_ERR_ARG; }
+  if (!c->tf_state) GPE_CU(c, cudaMalloc(&c->tf_state, 2 * sizeof(double)));
+  // bracket: S(vmin) = 0 < 1 and S(vmax + eta / (h^d N)) >= 1
+  const double br[2] = {c->vmin, c->vmax + c->prob.eta / (c->weight * (double)c->N)};
+  GPE_CU(c, cudaMemcpyAsync(c->tf_state, br, sizeof(br), cudaMemcpyHostToDevice, c->st));
+  const double* V64 = static_cast<const double*>(c->pb[1].V);
+  for (int it = 0; it < 120; ++it)  // halves the bracket each time: far below one ulp of mu
+    GPE_CU(c, launch_tf_bisect(V64, c->N, c->weight, c->prob.eta, c->tf_state, c->partials, c->ticket, c->st));
+  const bool dev = is_device_ptr(phi_out);
+  void* dst = dev ? phi_out : c->pb[1].phi;
+  GPE_CU(c, launch_tf_fill(V64, c->N, c->prob.eta, c->tf_state, dst, c->st));
+  if (!dev) GPE_CU(c, cudaMemcpyAsync(phi_out, dst, 16 * (size_t)c->N, cudaMemcpyDeviceToHost, c->st));
+  double st[2];
+  GPE_CU(c, cudaMemcpyAsync(st, c->tf_state, sizeof(st), cudaMemcpyDeviceToHost, c->st));
+  GPE_CU(c, cudaStreamSynchronize(c->st));
+  if (mu_out) *mu_out = 0.5 * (st[0] + st[1]);
+  return GPE_OK;
+}
 
 // P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
 static gpe_status run_PC(gpe_ctx* c, const IterBufs& b, const void* r, double alpha, void* out, Ctl* ctl,
@@ -867,7 +895,7 @@ static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
   h.max_iter = o.max_iter; h.max_backtracks = o.max_backtracks; h.cg = o.cg; h.stall_window = o.stall_window;
   h.log = log_cap ? c->log_dev : nullptr; h.log_cap = log_cap; h.log_len = 0;
   h.restart = 1; h.anchor_res = 1e300; h.anchor_iter = 0;
-  h.pc_kind = o.precond; h.beta_rule = o.beta_rule;
+  h.pc_kind = o.precond; h.beta_rule = o.beta_rule; h.line_search = o.line_search;
   double k2 = 0.0;  // max over the grid of |k|^2 / 2 (corner mode -M/2 on every axis)
   for (int i = 0; i < c->dim; ++i) {
     const double km = 0.5 * c->n[i] * M_PI / c->prob.L[i];
@@ -880,7 +908,7 @@ static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
 
 static gpe_status check_opts(gpe_solve_opts& o, std::string& err) {
   if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1 || o.precond < 0 ||
-      o.precond > 5 || o.beta_rule < 0 || o.beta_rule > 1) {
+      o.precond > 5 || o.beta_rule < 0 || o.beta_rule > 1 || o.line_search < 0 || o.line_search > 1) {
     err = "invalid solve options";
     return GPE_ERR_ARG;
   }

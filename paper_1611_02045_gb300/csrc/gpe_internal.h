@@ -22,6 +22,7 @@ struct Ctl {
   int pc_kind;   // preconditioner: 0 P_C (symmetric combined), 1 P_Delta, 2 P_V, 3 P_C1 = P_V P_Delta,
                  // 4 P_C2 = P_Delta P_V, 5 none
   int beta_rule; // 0 Polak-Ribiere beta+ (eq. CG:PR), 1 Fletcher-Reeves (eq. CG:FR)
+  int line_search;  // 0 model step theta_0 + backtracking; 1 Newton on the exact step polynomial from theta_0
   // ---- loop state ----
   int iter;        // n (global over both phases)
   int iter_phase0; // value of iter when this phase started
@@ -207,6 +208,14 @@ cudaError_t launch_batch_final(const void* phids, void* phi128, long long n, con
 cudaError_t launch_batch_gate64(Ctl* ctl, unsigned long long cond, cudaStream_t st);
 // Set the cluster solve kernel's attributes for grid size M (before capture).
 cudaError_t prepare_cluster_solve(int M);
+
+// Thomas-Fermi initial data (eq. TF_App): mu solving h^d sum max(mu - V, 0) / eta = 1
+// by bisection (state[0] = lo, state[1] = hi on entry; each launch halves the
+// bracket), then phi = sqrt(max(mu - V, 0) / eta) as complex128.
+cudaError_t launch_tf_bisect(const double* V, long long n, double weight, double eta, double* state,
+                             double* partials, unsigned* ticket, cudaStream_t st);
+cudaError_t launch_tf_fill(const double* V, long long n, double eta, const double* state, void* phi128,
+                           cudaStream_t st);
 
 // grad_phi <- 2 weight grad_phi (in place), grad_V = weight |phi|^2 (float64);
 // prec 0 complex64, 1 complex128; null outputs are skipped.

@@ -124,6 +124,59 @@ cudaError_t launch_d2f(const double* src, float* dst, long long n, cudaStream_t 
   return cudaGetLastError();
 }
 
+// One bisection step for the Thomas-Fermi chemical potential (eq. TF_App with
+// mu fixed by the normalisation ||phi^TF|| = 1): S(mid) = h^d sum max(mid - V, 0) / eta
+// with mid = (lo + hi) / 2; the last block to finish replaces lo (S < 1) or hi.
+constexpr int kTfThreads = 256;
+__global__ void __launch_bounds__(kTfThreads) k_tf_bisect(const double* __restrict__ V, long long n, double weight,
+                                                         double eta, double* state, double* __restrict__ partials,
+                                                         unsigned* ticket) {
+  __shared__ double sm[kTfThreads / 32];
+  __shared__ int s_last;
+  const double mid = 0.5 * (__ldcg(state) + __ldcg(state + 1));  // written by the previous launch
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += fmax(mid - V[i], 0.0);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kTfThreads / 32; ++w) b += sm[w];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(partials + b);
+  if (weight * tot / eta < 1.0) state[0] = mid;
+  else state[1] = mid;
+  *ticket = 0u;
+}
+cudaError_t launch_tf_bisect(const double* V, long long n, double weight, double eta, double* state,
+                             double* partials, unsigned* ticket, cudaStream_t st) {
+  long long g = (n + 8LL * kTfThreads - 1) / (8LL * kTfThreads);
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  k_tf_bisect<<<(int)g, kTfThreads, 0, st>>>(V, n, weight, eta, state, partials, ticket);
+  return cudaGetLastError();
+}
+
+__global__ void k_tf_fill(const double* __restrict__ V, long long n, double eta, const double* state,
+                          double2* __restrict__ phi) {
+  const double mu = 0.5 * (__ldcg(state) + __ldcg(state + 1));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    phi[i] = make_double2(sqrt(fmax(mu - V[i], 0.0) / eta), 0.0);
+}
+cudaError_t launch_tf_fill(const double* V, long long n, double eta, const double* state, void* phi128,
+                           cudaStream_t st) {
+  k_tf_fill<<<grid_for(n), 256, 0, st>>>(V, n, eta, state, (double2*)phi128);
+  return cudaGetLastError();
+}
+
 // Epilogue of gpe_energy_grad: grad_phi <- 2 h^d H_phi phi in place (Section 2,
 // nabla E = 2 H_phi phi, h^d converting to the coefficient vector) and
 // grad_V = h^d |phi|^2.  Either output may be null.

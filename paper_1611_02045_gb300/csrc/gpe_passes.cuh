@@ -309,6 +309,32 @@ __device__ __forceinline__ double delta_E(double s, double cth, double R, double
 // asum[0]: 0 Re<H phi,p>, 1 <p,A_x p>+<p,V p>, 2 |p|^2, 3 u v, 4 v^2, 5 u w,
 //          6 v w, 7 w^2, 8 v    (u = |phi|^2, v = Re(conj(phi) p), w = |p|^2)
 // asum[ax>0][1]: <p, A_ax p>
+// Newton's method on d/dt of the step polynomial delta_E (closed-form first
+// and second derivatives, with A = aqq - lam, B = eta/2 (U0 + W2),
+// C = eta/2 (4 V2 + 2 UW), D = 2 eta (VW - U1)) from the model step t0; t0 is
+// kept when the curvature is not positive or the iterate leaves (0, pi/2].
+static __device__ double exact_step(double t0, double R, double aqq, double lam, double eta, double U0, double U1,
+                                    double V2, double UW, double VW, double W2) {
+  const double A = aqq - lam, B = 0.5 * eta * (U0 + W2), C = 0.5 * eta * (4.0 * V2 + 2.0 * UW);
+  const double D = 2.0 * eta * (VW - U1);
+  double t = t0;
+  for (int it = 0; it < 30; ++it) {
+    double s, c, s2, c2, s4, c4;
+    sincos(t, &s, &c);
+    sincos(2.0 * t, &s2, &c2);
+    sincos(4.0 * t, &s4, &c4);
+    const double d1 = 2.0 * R * c2 + A * s2 + 4.0 * B * s * s * s * c + 0.5 * C * s4 + D * (3.0 * c * c * s * s - s * s * s * s);
+    const double d2 = -4.0 * R * s2 + 2.0 * A * c2 + 4.0 * B * (3.0 * s * s * c * c - s * s * s * s) + 2.0 * C * c4 +
+                      D * (6.0 * c * s * (c * c - s * s) - 4.0 * s * s * s * c);
+    if (!(d2 > 0.0)) return t0;
+    const double dt = d1 / d2;
+    t -= dt;
+    if (!(t > 0.0 && t <= 1.5707963267948966)) return t0;
+    if (fabs(dt) <= 1e-15 * fabs(t)) break;
+  }
+  return t;
+}
+
 static __device__ void finalize_A(Ctl* c, const Fin& a, bool writer) {
   const double w = a.weight;
   const double* s0 = c->asum[0];
@@ -324,6 +350,7 @@ static __device__ void finalize_A(Ctl* c, const Fin& a, bool writer) {
   const double eta = a.eta, lam = c->lam, U0 = c->U0;
   const double curv = aqq + eta * UW + 2.0 * eta * V2 - lam;
   double th = (curv > 0.0) ? -R / curv : c->theta_default;
+  if (c->line_search == 1) th = exact_step(th, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);
   double sn, cs;
   step_sincos(th, &sn, &cs);
   double dE = delta_E(sn, cs, R, aqq, lam, eta, U0, U1, V2, UW, VW, W2);

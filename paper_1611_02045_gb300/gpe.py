@@ -21,6 +21,7 @@ GPE_OK, GPE_ERR_ARG, GPE_ERR_CUDA, GPE_ERR_NOT_CONVERGED, GPE_ERR_NONFINITE, GPE
 GPE_FP64, GPE_MIXED = 0, 1
 GPE_PRECOND_C, GPE_PRECOND_DELTA, GPE_PRECOND_V, GPE_PRECOND_C1, GPE_PRECOND_C2, GPE_PRECOND_NONE = range(6)
 GPE_BETA_PR, GPE_BETA_FR = 0, 1
+GPE_LINE_MODEL, GPE_LINE_EXACT = 0, 1
 GPE_LOG_FIELDS = 12
 LOG_COLUMNS = ("n", "phase", "E", "lam", "res_inf", "res_l2", "alpha", "beta", "theta", "dE",
                "fallback", "backtracks")
@@ -38,7 +39,7 @@ class gpe_solve_opts(C.Structure):
                 ("theta_default", C.c_double), ("max_backtracks", C.c_int), ("cg", C.c_int),
                 ("stall_window", C.c_int), ("switch_res", C.c_double), ("max_iter_lo", C.c_int),
                 ("use_graph", C.c_int), ("refine_restart", C.c_int), ("precond", C.c_int),
-                ("beta_rule", C.c_int)]
+                ("beta_rule", C.c_int), ("line_search", C.c_int)]
 
 
 class gpe_report(C.Structure):
@@ -63,7 +64,8 @@ _lib = None
 EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H", "gpe_apply_H_batch", "gpe_precond",
             "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
             "gpe_pcg_solve", "gpe_last_error", "gpe_batch_create", "gpe_batch_solve", "gpe_batch_destroy",
-            "gpe_batch_last_error", "gpe_autotune", "gpe_set_plan", "gpe_get_plan", "gpe_batch_autotune")
+            "gpe_batch_last_error", "gpe_autotune", "gpe_set_plan", "gpe_get_plan", "gpe_batch_autotune",
+            "gpe_thomas_fermi")
 MODE_NAMES = ("complex64", "fp64", "refinement")
 _STRING_RETURNING = ("gpe_last_error", "gpe_batch_last_error")
 
@@ -101,6 +103,7 @@ def lib():
         L.gpe_set_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.gpe_get_plan.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.gpe_batch_autotune.argtypes = [vp, C.c_int]
+        L.gpe_thomas_fermi.argtypes = [vp, vp, C.POINTER(C.c_double)]
         for name in EXPORTED:
             if name not in _STRING_RETURNING:
                 getattr(L, name).restype = C.c_int
@@ -201,6 +204,12 @@ class Context:
                  for m in range(3) if r.E[m][0]}
         return dict(cached=bool(r.cached), candidates=r.candidates, us_before=list(r.us_before),
                     us_after=list(r.us_after), plans=plans)
+
+    def thomas_fermi(self, phi_out):
+        """gpe_thomas_fermi: fills phi_out (complex128, host or device); returns mu."""
+        mu = C.c_double(0.0)
+        self._check(lib().gpe_thomas_fermi(self._ctx, _addr(phi_out), C.byref(mu)))
+        return mu.value
 
     def set_plan(self, mode, axis, E, width):
         return self._check(lib().gpe_set_plan(self._ctx, int(mode), int(axis), int(E), int(width)))
