@@ -436,6 +436,48 @@ def thomas_fermi_state(prob):
 
 
 # --------------------------------------------------------------------------
+# Spectral interpolation for multigrid continuation (Section 6)
+# --------------------------------------------------------------------------
+
+
+def interpolate_axis(f, axis, Mf):
+    """Trigonometric interpolation of f along `axis` from Mc to Mf >= Mc points
+    on the same periodic interval: the interpolant
+        g(x) = (1/Mc) sum_p F_p e^{i xi_p (x + L)},  F = DFT_Mc(f),
+    with the Nyquist term F_{-Mc/2} shared equally by the modes -Mc/2 and +Mc/2
+    (so that real data interpolate to real data), sampled at the Mf points."""
+    Mc = f.shape[axis]
+    if Mf == Mc:
+        return f.copy()
+    F = np.fft.fft(f, axis=axis)
+    shape = list(f.shape)
+    shape[axis] = Mf
+    G = np.zeros(shape, dtype=complex)
+    h = Mc // 2
+
+    def sl(a, b):
+        idx = [slice(None)] * f.ndim
+        idx[axis] = slice(a, b)
+        return tuple(idx)
+
+    G[sl(0, h)] = F[sl(0, h)]
+    G[sl(Mf - h + 1, Mf)] = F[sl(h + 1, Mc)]
+    G[sl(h, h + 1)] = 0.5 * F[sl(h, h + 1)]
+    G[sl(Mf - h, Mf - h + 1)] = 0.5 * F[sl(h, h + 1)]
+    return np.fft.ifft(G, axis=axis) * (Mf / Mc)
+
+
+def interpolate(prob_c, phi_c, prob_f):
+    """phi_c on the grid of prob_c interpolated onto the grid of prob_f (same
+    domain, each size a multiple of the coarse one), axis by axis."""
+    assert tuple(prob_c.L) == tuple(prob_f.L)
+    g = phi_c
+    for i in range(prob_c.dim):
+        g = interpolate_axis(g, prob_c.dim - 1 - i, prob_f.n[i])  # numpy axis of physical axis i
+    return g
+
+
+# --------------------------------------------------------------------------
 # Derivatives (Section 2: gradient, Hessian, tangent space of the sphere)
 # --------------------------------------------------------------------------
 

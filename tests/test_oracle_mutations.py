@@ -31,6 +31,7 @@ QUICK_PINS = [
     P.test_P6_preconditioner_variants_adjointness,
     P.test_P5_line_search_derivatives_match_differences,
     P.test_P5_exact_step_minimises_the_energy_along_the_geodesic,
+    lambda: P.test_P14_interpolation_is_exact_for_band_limited_fields((16, 8), (32, 16)),
 ]
 
 
@@ -160,6 +161,21 @@ def _dderiv_wrong_quartic(m, eta, theta):
     return d1 - 2.0 * B * s_ ** 3 * c, d2
 
 
+def _interp_nyquist_unsplit(f, axis, Mf):
+    Mc = f.shape[axis]
+    if Mf == Mc:
+        return f.copy()
+    F = np.fft.fft(f, axis=axis)
+    shape = list(f.shape)
+    shape[axis] = Mf
+    G = np.zeros(shape, dtype=complex)
+    h = Mc // 2
+    idx = lambda a, b: tuple(slice(a, b) if k == axis else slice(None) for k in range(f.ndim))  # noqa: E731
+    G[idx(0, h)] = F[idx(0, h)]
+    G[idx(Mf - h, Mf)] = F[idx(h, Mc)]  # Nyquist kept at -Mc/2 only
+    return np.fft.ifft(G, axis=axis) * (Mf / Mc)
+
+
 MUTATIONS = {
     "Lz_sign": ("Lz", _lz_wrong_sign),
     "Lz_axes": ("Lz", _lz_swapped_axes),
@@ -178,6 +194,7 @@ MUTATIONS = {
     "pc_c2_as_c1": ("apply_preconditioner", _c2_as_c1),
     "pc_v_sqrt": ("apply_preconditioner", _pv_sqrt),
     "line_deriv_quartic": ("delta_energy_derivatives", _dderiv_wrong_quartic),
+    "interp_nyquist": ("interpolate_axis", _interp_nyquist_unsplit),
 }
 
 

@@ -494,3 +494,62 @@ def test_P13_thomas_fermi_mu_matches_the_continuum_closed_form_3d():
     mu = O.thomas_fermi_mu(p)
     want = (15.0 * eta * g[0] * g[1] * g[2] / (16.0 * np.sqrt(2.0) * np.pi)) ** 0.4
     assert abs(mu - want) < 2e-3 * want
+
+
+# ---------------------------------------------------------------- P14: spectral interpolation
+def _band_limited(n, L, modes):
+    m = I.mesh(n, L)
+    f = np.zeros(m[0].shape, dtype=complex)
+    for k, (coef, ks) in enumerate(modes):
+        phase = sum(kk * np.pi / Li * (xi + Li) for kk, xi, Li in zip(ks, m, L))
+        f = f + coef * np.exp(1j * phase)
+    return f
+
+
+@pytest.mark.parametrize("nc,nf", [((16, 8), (32, 16)), ((8, 8, 8), (16, 16, 16)), ((16, 16), (64, 64))])
+def test_P14_interpolation_is_exact_for_band_limited_fields(nc, nf):
+    """A field made of Fourier modes |p| < Mc/2 (and a cosine at the coarse
+    Nyquist frequency, which the symmetric split reproduces) is interpolated
+    exactly: the result equals the same analytic field sampled on the fine grid."""
+    L = tuple([4.0, 5.0, 3.0][: len(nc)])
+    modes = [(1.0 + 0.5j, [1] * len(nc)), (0.3, [-(nc[0] // 2) + 1] + [2] * (len(nc) - 1)),
+             (-0.7j, [3] + [-1] * (len(nc) - 1))]
+    pc = O.Problem(nc, L, 1.0, 0.0, np.zeros(I.shape_of(nc)))
+    pf = O.Problem(nf, L, 1.0, 0.0, np.zeros(I.shape_of(nf)))
+    fc = _band_limited(nc, L, modes)
+    # a cosine at the coarse Nyquist frequency along x (cos(Mc/2 * pi/L * (x + L)))
+    mc = I.mesh(nc, L)
+    mf = I.mesh(nf, L)
+    fc = fc + 0.4 * np.cos(nc[0] // 2 * np.pi / L[0] * (mc[0] + L[0]))
+    want = _band_limited(nf, L, modes) + 0.4 * np.cos(nc[0] // 2 * np.pi / L[0] * (mf[0] + L[0]))
+    got = O.interpolate(pc, fc, pf)
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_P14_interpolation_keeps_coarse_values_and_matches_the_trigonometric_sum():
+    """On a tiny grid: the fine values at the coarse points are the coarse
+    values, and every fine value equals the brute-force trigonometric sum."""
+    nc, nf, L = (8, 4), (16, 8), (2.0, 3.0)
+    pc = O.Problem(nc, L, 1.0, 0.0, np.zeros(I.shape_of(nc)))
+    pf = O.Problem(nf, L, 1.0, 0.0, np.zeros(I.shape_of(nf)))
+    fc = I.random_field(61, nc, L)
+    got = O.interpolate(pc, fc, pf)
+    assert np.max(np.abs(got[::2, ::2] - fc)) < 1e-13
+    xc, yc = pc.coord(0), pc.coord(1)
+    xs, ys = pf.coord(0).ravel(), pf.coord(1).ravel()
+
+    def weight(p, M):  # Nyquist shared by -M/2 and +M/2
+        return 0.5 if abs(p) == M // 2 else 1.0
+
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            tot = 0.0
+            for py in range(-nc[1] // 2, nc[1] // 2 + 1):
+                for px in range(-nc[0] // 2, nc[0] // 2 + 1):
+                    w = weight(px, nc[0]) * weight(py, nc[1])
+                    # coefficient F_p of the coarse DFT (index p mod M)
+                    e = np.exp(-1j * (px * np.pi / L[0] * (xc + L[0]) + py * np.pi / L[1] * (yc + L[1])))
+                    Fp = np.sum(fc * e)
+                    tot += w * Fp * np.exp(1j * (px * np.pi / L[0] * (x + L[0]) + py * np.pi / L[1] * (y + L[1])))
+            tot /= nc[0] * nc[1]
+            assert abs(tot - got[j, i]) < 1e-12, (i, j)
