@@ -278,6 +278,22 @@ gpe_status gpe_density_adjoint(gpe_ctx* ctx, const void* phi_dev, const double* 
  * Synchronises the stream.  Errors: GPE_ERR_ARG (eta <= 0), GPE_ERR_CUDA. */
 gpe_status gpe_thomas_fermi(gpe_ctx* ctx, void* phi_out, double* mu_out);
 
+/* Spectral interpolation for multigrid continuation (Section 6: the ground
+ * state on M_p points per axis is interpolated onto M_{p+1} = 2 M_p points and
+ * used as the initial data there).  Along every axis where fine->n = 2 coarse->n,
+ * each line is replaced by the samples at the fine points of its
+ * trigonometric interpolant (1/Mc) sum_p F_p e^{i xi_p (x + L)}, F = DFT(line),
+ * with the Nyquist coefficient shared equally by the modes -Mc/2 and +Mc/2;
+ * axes with equal sizes are copied.  Complex128 throughout.
+ *  coarse, fine : contexts on the same domain (equal L), same dimension, each
+ *                 fine axis equal to or twice the coarse one (coarse axes
+ *                 refined: at most 256 points).
+ *  phi_c  : complex128 coarse field, host or device.
+ *  phi_f  : complex128 fine field, host or device, not overlapping phi_c.
+ * Uses the fine context's stream and work buffers; synchronises.  Errors:
+ * GPE_ERR_ARG, GPE_ERR_UNSUPPORTED, GPE_ERR_CUDA (messages on fine). */
+gpe_status gpe_interpolate(gpe_ctx* coarse, const void* phi_c, gpe_ctx* fine, void* phi_f);
+
 /* Ground state by Algorithm 2 (PCG) with the symmetric combined
  * preconditioner P_C, the Polak-Ribiere coefficient beta = max(beta_PR, 0)
  * (eq. CG:PR), the descent check of Section 5.2, the step-size heuristic and

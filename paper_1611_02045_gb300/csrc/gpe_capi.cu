@@ -504,6 +504,68 @@ extern "C" gpe_status gpe_thomas_fermi(gpe_ctx* c, void* phi_out, double* mu_out
   return GPE_OK;
 }
 
+extern "C" gpe_status gpe_interpolate(gpe_ctx* cc, const void* phi_c, gpe_ctx* cf, void* phi_f) {
+  if (!cc || !cf) return GPE_ERR_ARG;
+  if (!phi_c || !phi_f) { cf->err = "null field pointer"; return GPE_ERR_ARG; }
+  if (cc->dim != cf->dim) { cf->err = "coarse and fine grids differ in dimension"; return GPE_ERR_ARG; }
+  for (int i = 0; i < cf->dim; ++i) {
+    const bool same_l = std::fabs(cc->prob.L[i] - cf->prob.L[i]) <= 1e-12 * std::fabs(cf->prob.L[i]);
+    if (!same_l || !(cf->n[i] == cc->n[i] || cf->n[i] == 2 * cc->n[i])) {
+      cf->err = "the fine grid must cover the same domain with n or 2n points per axis";
+      return GPE_ERR_ARG;
+    }
+    if (cf->n[i] == 2 * cc->n[i] && cc->n[i] > 256) { cf->err = "coarse axes above 256 points"; return GPE_ERR_UNSUPPORTED; }
+  }
+  cudaStream_t st = cf->st;
+  GPE_CU(cf, cudaStreamSynchronize(cc->st));
+  const double2* src = static_cast<const double2*>(phi_c);
+  if (!is_device_ptr(phi_c)) {
+    GPE_CU(cf, cudaMemcpyAsync(cc->pb[1].phi, phi_c, 16 * (size_t)cc->N, cudaMemcpyHostToDevice, st));
+    src = static_cast<const double2*>(cc->pb[1].phi);
+  }
+  const bool out_dev = is_device_ptr(phi_f);
+  // ping-pong through the fine context's work fields, the last stage into the destination
+  double2* bufs[2] = {static_cast<double2*>(cf->pb[1].t), static_cast<double2*>(cf->pb[1].s)};
+  double2* dst_final = out_dev ? static_cast<double2*>(phi_f) : static_cast<double2*>(cf->pb[1].phi);
+  int last = -1;
+  for (int i = 0; i < cf->dim; ++i)
+    if (cf->n[i] != cc->n[i]) last = i;
+  long long nx = cc->n[0], ny = cc->n[1], nz = cf->dim == 3 ? cc->n[2] : 1;  // current extents
+  const double2* cur = src;
+  int pp = 0;
+  for (int ax = 0; ax < cf->dim; ++ax) {
+    if (cf->n[ax] == cc->n[ax]) continue;
+    const int Mc = cc->n[ax];
+    double2* nxt = (ax == last) ? dst_final : bufs[pp];
+    pp ^= 1;
+    InterpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = cur; a.out = nxt;
+    a.tw_c = static_cast<const double2*>(cc->pb[1].tw[ax]);
+    a.tw_f = static_cast<const double2*>(cf->pb[1].tw[ax]);
+    if (ax == 0) {
+      a.lines = ny * nz; a.inner_count = 1;
+      a.in_outer = Mc; a.out_outer = 2 * Mc; a.in_stride = a.out_stride = 1;
+    } else if (ax == 1) {
+      a.lines = nx * nz; a.inner_count = nx;
+      a.in_outer = (long long)Mc * nx; a.out_outer = 2LL * Mc * nx; a.in_inner = a.out_inner = 1;
+      a.in_stride = a.out_stride = nx;
+    } else {
+      a.lines = nx * ny; a.inner_count = nx * ny;
+      a.in_outer = a.out_outer = 0; a.in_inner = a.out_inner = 1;
+      a.in_stride = a.out_stride = nx * ny;
+    }
+    GPE_CU(cf, launch_interp(Mc, a, st));
+    cur = nxt;
+    if (ax == 0) nx *= 2; else if (ax == 1) ny *= 2; else nz *= 2;
+  }
+  if (last < 0)  // nothing to refine: a copy
+    GPE_CU(cf, cudaMemcpyAsync(dst_final, src, 16 * (size_t)cf->N, cudaMemcpyDeviceToDevice, st));
+  if (!out_dev) GPE_CU(cf, cudaMemcpyAsync(phi_f, dst_final, 16 * (size_t)cf->N, cudaMemcpyDeviceToHost, st));
+  GPE_CU(cf, cudaStreamSynchronize(st));
+  return GPE_OK;
+}
+
 // P_C passes: s = FFT_x(P_V^{1/2} r) -> (3D: FFT_y) -> core -> (3D: IFFT_y) -> P_V^{1/2} IFFT_x.
 static gpe_status run_PC(gpe_ctx* c, const IterBufs& b, const void* r, double alpha, void* out, Ctl* ctl,
                          bool solver, cudaStream_t st) {

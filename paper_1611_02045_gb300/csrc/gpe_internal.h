@@ -217,6 +217,20 @@ cudaError_t launch_tf_bisect(const double* V, long long n, double weight, double
 cudaError_t launch_tf_fill(const double* V, long long n, double eta, const double* state, void* phi128,
                            cudaStream_t st);
 
+// Spectral interpolation onto a grid twice as fine along one axis
+// (gpe_interp.cu).  Line l = (outer, inner), inner < inner_count, starts at
+// outer * *_outer + inner * *_inner and its points are *_stride apart; Mc
+// coarse points in, 2 Mc fine points out, complex128.
+struct InterpArgs {
+  const double2* in;
+  double2* out;
+  long long lines, inner_count;
+  long long in_outer, out_outer, in_inner, out_inner, in_stride, out_stride;
+  const double2* tw_c;  // e^{-2 pi i m / Mc}
+  const double2* tw_f;  // e^{-2 pi i m / (2 Mc)}
+};
+cudaError_t launch_interp(int Mc, const InterpArgs& a, cudaStream_t st);
+
 // grad_phi <- 2 weight grad_phi (in place), grad_V = weight |phi|^2 (float64);
 // prec 0 complex64, 1 complex128; null outputs are skipped.
 cudaError_t launch_grad_epilogue(int prec, const void* phi, void* gphi, double* gV, long long n, double weight,

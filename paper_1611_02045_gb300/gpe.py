@@ -65,7 +65,7 @@ EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H"
             "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
             "gpe_pcg_solve", "gpe_last_error", "gpe_batch_create", "gpe_batch_solve", "gpe_batch_destroy",
             "gpe_batch_last_error", "gpe_autotune", "gpe_set_plan", "gpe_get_plan", "gpe_batch_autotune",
-            "gpe_thomas_fermi")
+            "gpe_thomas_fermi", "gpe_interpolate")
 MODE_NAMES = ("complex64", "fp64", "refinement")
 _STRING_RETURNING = ("gpe_last_error", "gpe_batch_last_error")
 
@@ -104,6 +104,7 @@ def lib():
         L.gpe_get_plan.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.gpe_batch_autotune.argtypes = [vp, C.c_int]
         L.gpe_thomas_fermi.argtypes = [vp, vp, C.POINTER(C.c_double)]
+        L.gpe_interpolate.argtypes = [vp, vp, vp, vp]
         for name in EXPORTED:
             if name not in _STRING_RETURNING:
                 getattr(L, name).restype = C.c_int
@@ -210,6 +211,12 @@ class Context:
         mu = C.c_double(0.0)
         self._check(lib().gpe_thomas_fermi(self._ctx, _addr(phi_out), C.byref(mu)))
         return mu.value
+
+    def interpolate_to(self, fine, phi_c, phi_f):
+        """gpe_interpolate: phi_c (this context's grid) onto fine's grid into phi_f."""
+        s = lib().gpe_interpolate(self._ctx, _addr(phi_c), fine._ctx, _addr(phi_f))
+        if s != GPE_OK:
+            raise GpeError(s, lib().gpe_last_error(fine._ctx).decode())
 
     def set_plan(self, mode, axis, E, width):
         return self._check(lib().gpe_set_plan(self._ctx, int(mode), int(axis), int(E), int(width)))

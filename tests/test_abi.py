@@ -123,6 +123,7 @@ def test_null_arguments(built_lib):
     assert lib.gpe_get_plan(None, 0, 0, None, None) == G.GPE_ERR_ARG
     assert lib.gpe_batch_autotune(None, 10) == G.GPE_ERR_ARG
     assert lib.gpe_thomas_fermi(None, None, None) == G.GPE_ERR_ARG
+    assert lib.gpe_interpolate(None, None, None, None) == G.GPE_ERR_ARG
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
