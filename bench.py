@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched sweep")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-kernel plans")
+    ap.add_argument("--plan", default="", help="E,width for every mode and axis instead of tuning (profiling runs)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the same pass kernels from a host loop instead of one graph with a device-side "
                          "loop (for ncu launch lists: ncu cannot profile kernel nodes of graphs with conditional "
@@ -196,7 +197,13 @@ def main():
     ctx = gpe.Context(n, L, w["eta"], w["omega"], w["V"], prec=gpe.GPE_MIXED)
     # set-up, outside every timed region: the tuner picks the pass-kernel plans
     tune = None
-    if not args.no_autotune:
+    if args.plan:
+        E_, w_ = (int(v) for v in args.plan.split(","))
+        for m_ in (0, 1, 2):
+            for ax_ in range(len(n)):
+                ctx.set_plan(m_, ax_, E_, w_)
+        tune = {"plans": f"fixed E={E_}, width={w_}", "seconds": 0.0}
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         tune = ctx.autotune(iters=20)
         tune["seconds"] = time.perf_counter() - t0

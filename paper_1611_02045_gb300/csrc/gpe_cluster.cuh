@@ -223,14 +223,17 @@ __global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::
     {
       const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
       const int y = rank * R + l;
+      // row bases once: the per-q offsets q Tl below are compile-time constants
+      const C* frow = fs + l * M + t;
+      const T* Vrow = V + y * M + t;
+      C* orow = out + fb + (long long)y * M + t;
       C w[E];
       T m[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        const int x = t + q * Tl;
-        w[q] = fs[l * M + x];
-        const C ph = same ? w[q] : phi[fb + (long long)y * M + x];
-        m[q] = V[(long long)y * M + x] + eta * (ph.x * ph.x + ph.y * ph.y);
+        w[q] = frow[q * Tl];
+        const C ph = same ? w[q] : phi[fb + (long long)y * M + t + q * Tl];
+        m[q] = Vrow[q * Tl] + eta * (ph.x * ph.x + ph.y * ph.y);
       }
       auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
       line_dft<M, E, -1, true>(w, xs, si, t, tw);
@@ -243,9 +246,8 @@ __global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::
       line_dft<M, E, +1, true>(w, xs, si, t, tw);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        const int x = t + q * Tl;
-        const C v = fs[l * M + x];
-        out[fb + (long long)y * M + x] = cmk<C>(w[q].x + m[q] * v.x, w[q].y + m[q] * v.y);
+        const C v = frow[q * Tl];
+        orow[q * Tl] = cmk<C>(w[q].x + m[q] * v.x, w[q].y + m[q] * v.y);
       }
     }
     cl.sync();  // rows(k) of every CTA visible; t rows stored; y parts of k - 1 finished
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::
     {
       const int c = threadIdx.x % R, t = threadIdx.x / R;
       const int x = rank * R + c;
+      // row y = t + q Tl lives in CTA y / R at local row y % R
       C w[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) {
@@ -271,11 +274,11 @@ __global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::
         w[q] = cscale(w[q], (T(0.5) * ky * ky - om * xx * ky) * invM);
       }
       line_dft<M, E, +1>(w, xs, si, t, tw);
+      C* ocol = out + fb + (long long)t * M + x;
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        const long long g = fb + (long long)(t + q * Tl) * M + x;
-        const C o = __ldcg(&out[g]);  // t, stored by the row's owner before the barrier
-        out[g] = cadd(o, w[q]);
+        const C o = __ldcg(ocol + q * Tl * M);  // t, stored by the row's owner before the barrier
+        ocol[q * Tl * M] = cadd(o, w[q]);
       }
     }
   }
