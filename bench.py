@@ -38,10 +38,10 @@ METRIC = "ground states/sec to residual 1e-8 (256², 128³); H·φ GB/s vs HBM p
 UNIT = "ground_states/s"
 HPHI_BATCH = 512  # fields of 256x256 complex64 in the H phi roofline batch (268 MB in, 268 MB out)
 # DRAM bytes (read + write) of one cluster_apply_H_stream<float,256,16> launch over HPHI_BATCH
-# fields: an ncu capture of a 256-field launch of the same kernel measured 134.6 MB + 87.6 MB;
+# fields: an ncu capture of a 256-field launch of the same kernel measured 134.6 MB + 87.8 MB;
 # scaled by 512/256 fields (traffic grows in proportion to the fields).  Set to None when that
 # kernel changes.
-HPHI_TRAFFIC_PER_LAUNCH = int(2 * (134.565376e6 + 87.616256e6))
+HPHI_TRAFFIC_PER_LAUNCH = int(2 * (134.644736e6 + 87.815936e6))
 
 
 def parse():
