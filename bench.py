@@ -63,10 +63,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1611_02045_gb300.replicas import dist_env as _env
+    return _env()
 
 
 def cpu_cores():
@@ -242,12 +240,9 @@ def main():
         step_ms.append(ev0.elapsed_time(ev1))
     barrier()
     clk = clocks.stop()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    from paper_1611_02045_gb300.replicas import job_throughput, max_over_ranks
+    ms = max_over_ranks(statistics.mean(step_ms), dev)
+    value = job_throughput(ms, world)
     launches = 0
     for r in reps:
         it, lo, fp = r["iters"], r["iters_lo"], r["iters_fp64"]
@@ -274,7 +269,7 @@ def main():
         ctx.pcg_solve(phi_h.data_ptr(), opts, check=True)
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    e2e_val = job_throughput(max_over_ranks(statistics.mean(e2e_ms), dev), world)
 
     # ---------------- roofline: H phi on a batch of fields larger than L2 ----------------
     # HPHI_BATCH fields of the workload's grid (gpe_apply_H_batch: resident 16-CTA clusters

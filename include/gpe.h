@@ -176,11 +176,16 @@ gpe_status gpe_apply_H(gpe_ctx* ctx, const void* phi_dev, const void* f_dev, voi
  * Section 2 / eq. FFTdiscret), on nbatch fields stored one after another
  * (stride nx*ny elements), all with the context's V, eta and omega.  2D
  * contexts with nx == ny in [32, 256] only.  Each field is transformed by one
- * thread-block cluster entirely in distributed shared memory, so global
- * memory is read and written once per point.  phi_dev, f_dev, out_dev: device
- * arrays in working precision; f may equal phi; out must not overlap phi or
- * f.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other grids),
- * GPE_ERR_CUDA. */
+ * thread-block cluster (16 rows per CTA) in distributed shared memory, so
+ * global memory is read and written once per point (the output is written by
+ * the row phase and completed by the column phase while still in L2).  In
+ * single precision with n >= 64 and 16-byte aligned phi and f, the resident
+ * clusters loop over the fields and copy the next field's rows while
+ * transforming the current one (plan mode 3 of gpe_set_plan: E = 16, the
+ * default; E = 8 selects one field per cluster).  phi_dev, f_dev, out_dev:
+ * device arrays in working precision; f may equal phi; out must not overlap
+ * phi or f.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other
+ * grids), GPE_ERR_CUDA. */
 gpe_status gpe_apply_H_batch(gpe_ctx* ctx, int nbatch, const void* phi_dev, const void* f_dev, void* out_dev);
 
 /* out = P_C r = P_V^{1/2} P_Delta P_V^{1/2} r (eq. combinedP_12) with

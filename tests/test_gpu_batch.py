@@ -95,6 +95,29 @@ def test_stalled_refinement_is_completed_in_fp64(G):
     assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
 
 
+def test_batch_with_3d_instances(G):
+    """3D instances (complex64 phase as a loop node over the 3D pass kernels)
+    next to a 2D one: each reproduces its single-instance solve."""
+    specs = []
+    for n, L, eta, om, seed in [((32, 32, 32), (6.0, 6.0, 6.0), 200.0, 0.4, 7),
+                                ((16, 32, 16), (5.0, 6.0, 5.0), 50.0, 0.2, 8),
+                                ((64, 64), (8.0, 8.0), 100.0, 0.5, 9)]:
+        V = I.harmonic(n, L, [1.0, 1.0, 2.0][: len(n)])
+        G0 = I.anisotropic_gaussian(n, L, [1.0, 1.0, 2.0][: len(n)])
+        phi0 = I.perturbed(I.normalise(G0 * (1 + 0.5j * I.mesh(n, L)[0]), n, L), seed, n, L)
+        specs.append(dict(n=n, L=L, eta=eta, omega=om, V=V, prec=G.GPE_MIXED, phi0=phi0))
+    opts = G.solve_opts_default()
+    with G.Batch(specs) as B:
+        phis = [dev(w["phi0"]) for w in specs]
+        s, reps = B.solve(phis, opts)
+    assert s == G.GPE_OK, reps
+    for i, w in enumerate(specs):
+        ph1, r1 = _single(G, w, opts)
+        assert reps[i]["iters"] == r1["iters"] and reps[i]["E"] == r1["E"], (i, reps[i], r1)
+        assert np.array_equal(host(phis[i]), ph1)
+        assert reps[i]["loop_kind"] == (3 if len(w["n"]) == 2 else 1)
+
+
 def test_batch_reports_each_instance_status(G):
     """A non-finite initial guess fails its own instance only; the others
     converge and the batch returns the failing status."""
