@@ -182,7 +182,7 @@ gpe_status gpe_apply_H(gpe_ctx* ctx, const void* phi_dev, const void* f_dev, voi
  * single precision with n >= 64 and 16-byte aligned phi and f, the resident
  * clusters loop over the fields and copy the next field's rows while
  * transforming the current one (plan mode 3 of gpe_set_plan: E = 16, the
- * default; E = 8 selects one field per cluster).  phi_dev, f_dev, out_dev:
+ * default, with 16 or 32 rows per CTA; E = 8 selects one field per cluster).  phi_dev, f_dev, out_dev:
  * device arrays in working precision; f may equal phi; out must not overlap
  * phi or f.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other
  * grids), GPE_ERR_CUDA. */
@@ -379,7 +379,11 @@ gpe_status gpe_autotune(gpe_ctx* ctx, int iters, int use_cache, gpe_tune_report*
 /* Set / read the plan of (mode, axis).  gpe_set_plan rejects plans the kernels
  * cannot run (E not 4 or 8, E = 4 below M = 32, width not a power of two, more
  * threads than the mode's kernels allow, too much shared memory, more blocks
- * than the context's reduction buffers) with GPE_ERR_ARG. */
+ * than the context's reduction buffers) with GPE_ERR_ARG.  Mode 3, axis 0 is
+ * the cluster kernel of gpe_apply_H_batch: E = 8 (one field per cluster, 16
+ * rows per CTA) or E = 16 (the streaming form, single precision, n >= 64)
+ * with width = rows per CTA, 16 (a cluster of n/16 CTAs) or 32 (n/32 CTAs,
+ * so an 8-CTA cluster at n = 256). */
 gpe_status gpe_set_plan(gpe_ctx* ctx, int mode, int axis, int E, int width);
 gpe_status gpe_get_plan(const gpe_ctx* ctx, int mode, int axis, int* E, int* width);
 

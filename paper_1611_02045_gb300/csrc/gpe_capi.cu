@@ -70,6 +70,7 @@ struct gpe_ctx {
   PassPlan plan[3];      // default plan per axis (E = 8, heuristic widths)
   PassPlan mplan[3][3];  // plan used per launch mode [mode][axis] (the default, or the tuner's choice)
   int partials_cap = 0;  // blocks the reduction partials buffer holds
+  int hbatch_rows = 16;  // rows per CTA of its streaming form (plan mode 3 width: 16 or 32)
   int hbatch_E = 8;      // values per thread of gpe_apply_H_batch's cluster kernel (plan mode 3):
                          // 16 (streaming form) by default in single precision for n >= 64
   double vmax = 0.0;  // max V on the grid
@@ -415,6 +416,7 @@ extern "C" gpe_status gpe_apply_H_batch(gpe_ctx* c, int nbatch, const void* phi,
   a.xi = b.xi[0]; a.xiy = b.xi[1]; a.xc = b.xc[0]; a.yc = b.xc[1]; a.tw = b.tw[0]; a.V = b.V;
   a.phi = phi; a.f = f; a.out = out;
   a.E = c->hbatch_E;
+  a.rows = c->hbatch_rows;
   GPE_CU(c, launch_cluster_apply_H(prec, a, c->st));
   return GPE_OK;
 }
@@ -1036,11 +1038,13 @@ static bool hbatch_eligible(const gpe_ctx* c) {
 extern "C" gpe_status gpe_set_plan(gpe_ctx* c, int mode, int axis, int E, int width) {
   if (!c) return GPE_ERR_ARG;
   if (mode == 3) {  // the cluster kernel of gpe_apply_H_batch: E only, width = rows per CTA
-    const bool ok = hbatch_eligible(c) && axis == 0 && width == 16 &&
+    // width: rows per CTA, 16; or 32 for the streaming form (E = 16, n >= 64)
+    const bool ok = hbatch_eligible(c) && axis == 0 && (width == 16 || (width == 32 && E == 16)) &&
                     (E == 8 || (E == 16 && c->work == 0 && c->n[0] >= 64));
     if (!ok) { c->err = "plan not supported by the batched H kernel"; return GPE_ERR_ARG; }
     GPE_CU(c, cudaStreamSynchronize(c->st));
     c->hbatch_E = E;
+    c->hbatch_rows = width;
     return GPE_OK;
   }
   if (!mode_available(c, mode)) { c->err = "launch mode not used by this context"; return GPE_ERR_ARG; }
@@ -1055,7 +1059,7 @@ extern "C" gpe_status gpe_set_plan(gpe_ctx* c, int mode, int axis, int E, int wi
 extern "C" gpe_status gpe_get_plan(const gpe_ctx* c, int mode, int axis, int* E, int* width) {
   if (c && E && width && mode == 3 && axis == 0 && hbatch_eligible(c)) {
     *E = c->hbatch_E;
-    *width = 16;
+    *width = c->hbatch_E == 16 ? c->hbatch_rows : 16;
     return GPE_OK;
   }
   if (!c || !E || !width || mode < 0 || mode > 2 || axis < 0 || axis >= c->dim) return GPE_ERR_ARG;

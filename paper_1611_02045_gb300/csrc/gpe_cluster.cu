@@ -19,11 +19,20 @@ cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStr
     // when the fields are 16-byte aligned, else one field per cluster
     bool ok = false;
     cudaError_t e = cudaSuccess;
-    switch (a.M) {
-      case 64: e = launch_cluster_apply_H_stream<float, 64, 16>(a, st, &ok); break;
-      case 128: e = launch_cluster_apply_H_stream<float, 128, 16>(a, st, &ok); break;
-      case 256: e = launch_cluster_apply_H_stream<float, 256, 16>(a, st, &ok); break;
-      default: return cudaErrorInvalidValue;
+    if (a.rows == 32) {
+      switch (a.M) {
+        case 64: e = launch_cluster_apply_H_stream<float, 64, 16, 32>(a, st, &ok); break;
+        case 128: e = launch_cluster_apply_H_stream<float, 128, 16, 32>(a, st, &ok); break;
+        case 256: e = launch_cluster_apply_H_stream<float, 256, 16, 32>(a, st, &ok); break;
+        default: return cudaErrorInvalidValue;
+      }
+    } else {
+      switch (a.M) {
+        case 64: e = launch_cluster_apply_H_stream<float, 64, 16, 16>(a, st, &ok); break;
+        case 128: e = launch_cluster_apply_H_stream<float, 128, 16, 16>(a, st, &ok); break;
+        case 256: e = launch_cluster_apply_H_stream<float, 256, 16, 16>(a, st, &ok); break;
+        default: return cudaErrorInvalidValue;
+      }
     }
     if (e != cudaSuccess || ok) return e;
     switch (a.M) {

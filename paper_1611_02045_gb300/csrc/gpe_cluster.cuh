@@ -40,6 +40,7 @@ struct ClusterHArgs {
   const void* f;     // operands (may equal phi)
   void* out;         // results
   int E;             // values per thread: 16 (single precision, M >= 64) or 8 (also when 0)
+  int rows;          // streaming form (E = 16): rows per CTA, 16 (also when 0) or 32
 };
 
 // Two CTAs per SM in single precision (two fields in flight per SM group).
@@ -177,11 +178,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // After the barrier of field k every CTA has finished the y part of field
 // k - 1, so the buffer that held rows(k - 1) is free for rows(k + 1).
 // Requires f (and phi) 16-byte aligned.
-template <typename T, int M, int EV>
-__global__ void __launch_bounds__((M / EV) * kClusterRows, ClusterMinBlocks<T>::value)
+// Rows per CTA RR: 16 (clusters of M/16 CTAs, two CTAs per SM) or 32 (clusters
+// of M/32 CTAs, one 512-thread CTA per SM at M = 256 with E = 16).
+template <typename T, int RR> struct StreamMinBlocks { static constexpr int value = RR == 16 ? ClusterMinBlocks<T>::value : 1; };
+
+template <typename T, int M, int EV, int RR>
+__global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
     cluster_apply_H_stream(ClusterHArgs a) {
   using C = cplx<T>;
-  constexpr int E = EV, Tl = M / EV, R = kClusterRows, LS = M + M / 16;
+  constexpr int E = EV, Tl = M / EV, R = RR, LS = M + M / 16;
   constexpr int NT = Tl * R;  // threads per CTA
   static_assert(Tl <= 32 && (32 % Tl) == 0, "a row's threads lie inside one warp");
   cg::cluster_group cl = cg::this_cluster();
@@ -320,15 +325,15 @@ cudaError_t launch_cluster_apply_H_one(const ClusterHArgs& a, cudaStream_t st) {
 // Streaming launcher: as many clusters as can be resident (at most one per
 // field); false in *ok when the kernel cannot be used (f or phi not 16-byte
 // aligned), so the caller launches the one-field-per-cluster form.
-template <typename T, int M, int EV>
+template <typename T, int M, int EV, int RR>
 cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st, bool* ok) {
   *ok = false;
   if ((reinterpret_cast<uintptr_t>(a.f) & 15u) != 0 || (reinterpret_cast<uintptr_t>(a.phi) & 15u) != 0) return cudaSuccess;
-  constexpr int R = kClusterRows;
+  constexpr int R = RR;
   const int csize = M / R;
   const int threads = (M / EV) * R;
   const size_t smem = (size_t)(2 * R * M + R * (M + M / 16)) * sizeof(cplx<T>);
-  auto kern = cluster_apply_H_stream<T, M, EV>;
+  auto kern = cluster_apply_H_stream<T, M, EV, RR>;
   static int max_clusters = -1;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3((unsigned)threads);

@@ -23,6 +23,7 @@ def main():
     ap.add_argument("--op", choices=["apply_H", "apply_H_batch", "precond", "energy", "solve"], default="apply_H")
     ap.add_argument("--batch", type=int, default=64, help="fields for --op apply_H_batch (2D grid)")
     ap.add_argument("--hbatch-E", type=int, default=0, help="values per thread of the batched H kernel (8, 16)")
+    ap.add_argument("--hbatch-rows", type=int, default=16, help="rows per CTA of its streaming form (16, 32)")
     ap.add_argument("--workload", default="fast256_2d", help="for --op solve")
     ap.add_argument("--max-iter", type=int, default=50, help="for --op solve")
     ap.add_argument("--switch-res", type=float, default=0.0, help="for --op solve (mixed)")
@@ -83,7 +84,7 @@ def main():
     ctx = gpe.Context(n, L, 100.0, 0.5, V, prec=prec)
     del V
     if a.hbatch_E:
-        ctx.set_plan(3, 0, a.hbatch_E, 16)
+        ctx.set_plan(3, 0, a.hbatch_E, a.hbatch_rows)
     dt = torch.complex128 if a.prec == "fp64" else torch.complex64
     g = torch.Generator(device=dev).manual_seed(1)
     nf = a.batch if a.op == "apply_H_batch" else 1

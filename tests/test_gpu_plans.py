@@ -206,8 +206,9 @@ def test_batched_H_kernel_plans_match_oracle(G, M, E):
         assert relmax(got[b], O.apply_H(po, phh[b], fh[b])) < 2e-5, b
 
 
+@pytest.mark.parametrize("rows", [16, 32])
 @pytest.mark.parametrize("M,nb", [(64, 150), (256, 37)])
-def test_streaming_batched_H_kernel_loops_over_fields(G, M, nb):
+def test_streaming_batched_H_kernel_loops_over_fields(G, M, nb, rows):
     """With E = 16 and 16-byte aligned fields the batched H kernel runs as
     resident clusters looping over the fields (rows of the next field copied
     while the current one's columns are transformed): more fields than
@@ -221,7 +222,8 @@ def test_streaming_batched_H_kernel_loops_over_fields(G, M, nb):
     ph_d, f_d = dev(phis, torch.complex64), dev(fs, torch.complex64)
     out = torch.empty_like(f_d)
     with G.Context(n, L, eta, om, V, prec=G.GPE_MIXED) as ctx:
-        ctx.set_plan(3, 0, 16, 16)
+        ctx.set_plan(3, 0, 16, rows)
+        assert ctx.get_plan(3, 0) == (16, rows)
         for rep in range(2):  # twice: the second launch starts from the first one's buffers
             out.fill_(float("nan"))
             ctx.apply_H_batch(nb, ph_d, f_d, out)
