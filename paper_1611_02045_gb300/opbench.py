@@ -31,7 +31,8 @@ def main():
                     help="for --op solve: the library default, the cluster-resident complex64 phase, the "
                          "persistent kernel, the graph with a device-side loop, or a host loop")
     ap.add_argument("--autotune", action="store_true", help="for --op solve: tune the pass-kernel plans first")
-    ap.add_argument("--plan", default="", help="for --op solve: E,width applied to every mode and axis")
+    ap.add_argument("--plan", default="",
+                    help="E,width applied to every axis (solve: every mode), or E,w/E,w[/E,w] per axis")
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
@@ -85,6 +86,11 @@ def main():
     del V
     if a.hbatch_E:
         ctx.set_plan(3, 0, a.hbatch_E, a.hbatch_rows)
+    if a.plan:
+        per = a.plan.split("/")
+        for ax in range(len(n)):
+            E, wd = (int(v) for v in per[ax if len(per) > 1 else 0].split(","))
+            ctx.set_plan(1 if prec == gpe.GPE_FP64 else 0, ax, E, wd)
     dt = torch.complex128 if a.prec == "fp64" else torch.complex64
     g = torch.Generator(device=dev).manual_seed(1)
     nf = a.batch if a.op == "apply_H_batch" else 1
@@ -116,7 +122,8 @@ def main():
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
-    print(json.dumps({"op": a.op, "grid": list(n), "fields": nf, "prec": a.prec, "points": N * nf, "ms": ms,
+    plan = [list(ctx.get_plan(1 if prec == gpe.GPE_FP64 else 0, ax)) for ax in range(len(n))]
+    print(json.dumps({"op": a.op, "grid": list(n), "fields": nf, "prec": a.prec, "plan": plan, "points": N * nf, "ms": ms,
                       "algorithmic_bytes_per_point": bytes_pt,
                       "effective_GBps": bytes_pt * N * nf / (ms * 1e-3) / 1e9}))
 
