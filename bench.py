@@ -13,7 +13,10 @@ phi already in device memory.  Alongside it the line reports:
   e2e           the same solve with phi in pinned HOST memory (H2D/D2H copies
                 inside the call and inside the timed region);
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload;
-  secondary     the 128^3 3D workload (eta = 5000, omega = 0.8), ground states/s.
+  secondary     the 128^3 3D workload (eta = 5000, omega = 0.8), ground states/s;
+  batch         the 96-instance parameter sweep in one graph launch, ground states/s;
+  libfft_baseline  the same workload solved in FP64 by plain PyTorch with
+                torch.fft (cuFFT), beside this library's FP64 single-instance solve.
 
 --impl reference runs the CPU oracle as the reference arm.
 """
@@ -53,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched sweep")
+    ap.add_argument("--no-libfft", action="store_true",
+                    help="skip the library-FFT baseline (torch.fft / cuFFT complex128 PCG_C) and the FP64 solve")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-kernel plans")
     ap.add_argument("--plan", default="", help="E,width for every mode and axis instead of tuning (profiling runs)")
     ap.add_argument("--no-graph", action="store_true",
@@ -361,6 +366,47 @@ def main():
                  "fp64_completions": int(sum(r["iters_fp64"] > 0 for r in breps))}
         del bphi, bphi0
 
+    # ---------------- GPU library baseline: the same FP64 solve with torch.fft (cuFFT) ----------------
+    # Reported beside this library's FP64 single-instance solve of the same workload (same algorithm,
+    # same stopping rule); neither is the headline, which is the mixed-precision solve above.
+    libfft = None
+    if not args.no_libfft and rank == 0:
+        from baseline.libfft_pcg import LibFFTPCG
+
+        def timed(fn):
+            l2_flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            b.synchronize()
+            return out, a.elapsed_time(b)
+
+        lb = LibFFTPCG(n, L, w["eta"], w["omega"], w["V"], device=dev)
+        lb.solve(w["phi0"], max_iter=20)  # warm-up: cuFFT plans, allocator
+        lrep, lms = timed(lambda: lb.solve(w["phi0"]))
+        ctx64 = gpe.Context(n, L, w["eta"], w["omega"], w["V"], prec=gpe.GPE_FP64)
+        if not args.no_autotune:
+            ctx64.autotune(iters=10)
+        p64_0 = torch.from_numpy(w["phi0"].copy()).to(dev)
+        p64 = torch.empty_like(p64_0)
+
+        def solve64():
+            p64.copy_(p64_0)
+            return ctx64.pcg_solve(p64, check=True)
+
+        solve64()  # warm-up (graph build)
+        r64, ms64 = timed(solve64)
+        ctx64.close()
+        libfft = {"kind": "plain PyTorch + torch.fft (cuFFT), complex128 PCG_C (baseline/libfft_pcg.py)",
+                  "workload": WORKLOAD, "value": 1000.0 / lms, "unit": UNIT, "ms_per_step": lms,
+                  "iters": lrep["iters"], "ms_per_iter": lms / max(lrep["iters"], 1), "status": lrep["status"],
+                  "E": lrep["E"], "res_inf": lrep["res_inf"],
+                  "gb300_fp64": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "iters": r64["iters"],
+                                 "ms_per_iter": ms64 / max(r64["iters"], 1), "E": r64["E"],
+                                 "res_inf": r64["res_inf"]}}
+        del lb, p64, p64_0
+
     # ---------------- CPU baseline (oracle, bounded sample) ----------------
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -397,6 +443,7 @@ def main():
             "cpu_baseline": cpu,
             "secondary": secondary,
             "batch": batch,
+            "libfft_baseline": libfft,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
