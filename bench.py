@@ -97,6 +97,22 @@ def oracle_sample(seconds=12.0, max_iters=400):
     return dt / max(rep["iters"], 1), rep["iters"]
 
 
+def oracle_naive_64():
+    """The naive-DFT oracle (explicit O(M^2) sums per line) solving the 64x64
+    workload c64_2d to ||r||_inf < 1e-8, and the FFT-backend oracle on the same
+    solve: (naive seconds, fft seconds, iterations)."""
+    from oracle import gpe_oracle as O
+    from paper_1611_02045_gb300 import inputs as I
+    w = I.workload("c64_2d")
+    out = []
+    for backend in ("naive", "fft"):
+        prob = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"], backend=backend)
+        t0 = time.perf_counter()
+        _, rep = O.pcg_solve(prob, w["phi0"], O.SolveOptions())
+        out.append((time.perf_counter() - t0, rep["iters"]))
+    return out[0][0], out[1][0], out[0][1]
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -414,6 +430,9 @@ def main():
         cpu = {"value": 1.0 / (t_it * iters_total), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{k} FP64 numpy PCG_C iterations of {WORKLOAD} ({t_it*1e3:.1f} ms/iteration, "
                          f"1 thread), scaled by the {iters_total} iterations of the GPU solve"}
+        t_naive, t_fft, it64 = oracle_naive_64()
+        cpu["naive_dft_64"] = {"workload": "c64_2d (64x64, complex128, ||r||_inf < 1e-8)", "iters": it64,
+                               "s_per_solve_naive_dft": t_naive, "s_per_solve_fft": t_fft, "cores": 1}
 
     if rank == 0:
         last = reps[-1]
