@@ -188,6 +188,34 @@ def test_hermitian_and_vortex_eigenfunction_on_gpu(G):
         assert abs(a - c) < 1e-12 * abs(a)
 
 
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_linear_trap_ground_state_closed_form(G, case, prec):
+    """Degenerate case with a closed form, independent of the oracle: eta = 0
+    in the trap V = 1/2 sum gamma_i^2 x_i^2 has the Gaussian ground state with
+    E = sum gamma_i / 2, and rotation below the trap frequency (omega < 1 about
+    z with gamma_x = gamma_y = 1) leaves it the ground state (its L_z value is
+    0; the states L_z = m cost m (1 - omega) more).  From a perturbed,
+    off-centre start the solver must reach E = d/2 (2D: 1; 3D with gamma =
+    (1, 1, 2): 2) to the tolerance of its precision."""
+    if case == "2d":
+        n, L, gam = (64, 64), (8.0, 8.0), [1.0, 1.0]
+    else:
+        n, L, gam = (32, 32, 32), (6.0, 6.0, 6.0), [1.0, 1.0, 2.0]
+    V = I.harmonic(n, L, gam)
+    m = I.mesh(n, L)
+    start = np.exp(-0.5 * sum(((x - 0.7) / 1.3) ** 2 for x in m)).astype(np.complex128) * (1.0 + 0.3 * (m[0] + 1j * m[1]))
+    phi0 = I.perturbed(start, 11, n, L, amp=1e-2)
+    E_exact = 0.5 * sum(gam)
+    with make(n, L, 0.0, 0.5, V, G.GPE_FP64 if prec == "fp64" else G.GPE_MIXED, G) as ctx:
+        phi = dev(phi0)
+        rep = ctx.pcg_solve(phi)
+    assert rep["status"] == G.GPE_OK, rep
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert abs(rep["E"] - E_exact) <= tol * E_exact, (rep["E"], E_exact)
+    assert abs(rep["lam"] - E_exact) <= 1e-6 * E_exact  # eta = 0: lambda = E
+
+
 # ------------------------------------------------------------------ solver
 def _workload_problem(name):
     w = I.workload(name)
