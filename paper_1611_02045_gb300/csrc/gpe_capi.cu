@@ -382,6 +382,9 @@ extern "C" const char* gpe_last_error(const gpe_ctx* c) { return c ? c->err.c_st
 static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, void* out, Ctl* ctl) {
   PassArgs a = base_args(c, prec, 0, prec);
   a.ctl = ctl; a.phi = phi; a.f = f; a.t = c->pb[prec].t;
+  // fields above 64 MB (beyond L2 with the operator's other arrays): the x pass
+  // prefetches the rows of the block one wave ahead (two blocks per SM)
+  if ((double)c->N * (prec == 0 ? 8.0 : 16.0) > 64.0 * 1024 * 1024) a.pf = 2 * c->nsm;
   GPE_CU(c, launch(prec, P_HX, a, c->st));
   for (int ax = 1; ax < c->dim; ++ax) {
     PassArgs b = base_args(c, prec, ax, prec);

@@ -88,6 +88,7 @@ struct PassArgs {
   long long outer_stride;  // strided: element stride of the outer index
   int ntx;         // strided: nx / tx
   int nblocks;     // grid size
+  int pf;          // contiguous H pass outside a solve: L2 prefetch of the rows of unit + pf (0: none)
   int solver;      // 1: inside a solve (uses ctl scalars, solver reductions)
   int last_axis;   // 1: this pass is the final one of its operator (runs the finaliser)
   double weight;   // h^d

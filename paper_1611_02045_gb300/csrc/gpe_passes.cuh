@@ -437,6 +437,8 @@ __device__ __forceinline__ const T* tab(const void* p) { return static_cast<cons
 // Max threads per block: 512 with single-precision transforms, 256 with double.
 template <typename T> struct MaxThreads { static constexpr int value = sizeof(T) == 8 ? 256 : 512; };
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename To, typename From>
 __device__ __forceinline__ cplx<To> cconv(From v) { return cmk<cplx<To>>((To)v.x, (To)v.y); }
 
@@ -472,6 +474,19 @@ __device__ __forceinline__ void xunit(const PassArgs& a, const Scal& S, long lon
     static_assert(sizeof(TF) == sizeof(TS), "H passes transform the state precision");
     const CS* __restrict__ phi = static_cast<const CS*>(a.phi);
     const CS* __restrict__ f = static_cast<const CS*>(a.f ? a.f : a.phi);
+    if (a.pf > 0 && unit + a.pf < a.nblocks) {
+      // fields larger than L2: the block about one wave later reads the rows of
+      // unit + pf; start bringing them (phi, f, V) into L2 now, 128-byte lines
+      const long long e0 = (unit + a.pf) * a.lpb * M;
+      const int nb = a.lpb * M * (int)sizeof(CS);
+      for (int off = threadIdx.x * 128; off < nb; off += blockDim.x * 128) {
+        prefetch_l2(reinterpret_cast<const char*>(phi + e0) + off);
+        if (a.f && a.f != a.phi) prefetch_l2(reinterpret_cast<const char*>(f + e0) + off);
+      }
+      const int nv = a.lpb * M * (int)sizeof(TS);
+      for (int off = threadIdx.x * 128; off < nv; off += blockDim.x * 128)
+        prefetch_l2(reinterpret_cast<const char*>(V + e0) + off);
+    }
     CS ph[E];
     TS vv[E];
     const bool retract = S.retract;
