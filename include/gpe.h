@@ -163,7 +163,9 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
  * [8,512], L <= 0, non-finite eta/omega), GPE_ERR_CUDA. */
 gpe_status gpe_create(const gpe_problem* prob, const double* V, void* stream, gpe_ctx** out);
 
-/* Release everything the context owns.  NULL is accepted. */
+/* Synchronise the context's stream, then release everything the context owns
+ * (device workspace, tables, graphs).  Caller-owned fields are untouched.
+ * NULL is accepted.  Always returns GPE_OK. */
 gpe_status gpe_destroy(gpe_ctx* ctx);
 
 /* out = H_phi f = -1/2 Delta f + V f + eta |phi|^2 f - omega L_z f
@@ -385,6 +387,11 @@ gpe_status gpe_autotune(gpe_ctx* ctx, int iters, int use_cache, gpe_tune_report*
  * with width = rows per CTA, 16 (a cluster of n/16 CTAs) or 32 (n/32 CTAs,
  * so an 8-CTA cluster at n = 256). */
 gpe_status gpe_set_plan(gpe_ctx* ctx, int mode, int axis, int E, int width);
+/* The plan in use for (mode, axis): *E values per thread and *width (lines per
+ * block on axis 0, tile columns on the others; rows per CTA for mode 3), host
+ * ints written by the call.  Errors: GPE_ERR_ARG (null pointers, mode outside
+ * 0..2, axis outside the grid, mode 3 on a context the batched H kernel does
+ * not take). */
 gpe_status gpe_get_plan(const gpe_ctx* ctx, int mode, int axis, int* E, int* width);
 
 /* ---- Batched solves ------------------------------------------------------
@@ -411,16 +418,25 @@ gpe_status gpe_batch_create(int count, const gpe_problem* probs, const double* c
  * restarts beta at the refinement and keeps no log).  reports: NULL or an
  * array of count reports.  The graph is built by the first call.  Synchronises
  * the stream.  Returns GPE_OK when every instance met the stopping rule, else
- * the first failing instance's status (each report carries its own). */
+ * the first failing instance's status (each report carries its own).  Errors:
+ * GPE_ERR_ARG (NULL batch or phi array or entry, invalid options),
+ * GPE_ERR_CUDA; the per-instance statuses are those of gpe_pcg_solve. */
 gpe_status gpe_batch_solve(gpe_batch* batch, void* const* phi_inout, const gpe_solve_opts* opts, gpe_report* reports);
 
+/* Synchronise the batch's stream and release the batch, its graph and every
+ * instance's context.  NULL is accepted.  Always returns GPE_OK. */
 gpe_status gpe_batch_destroy(gpe_batch* batch);
 
 /* gpe_autotune (with the process cache) on every instance's context; the
- * batch graph is rebuilt with the chosen plans by the next gpe_batch_solve. */
+ * batch graph is rebuilt with the chosen plans by the next gpe_batch_solve.
+ * Overwrites the instances' solver work buffers; synchronises the stream.
+ * Errors: GPE_ERR_ARG (NULL batch, iters < 1), GPE_ERR_CUDA (the message, read
+ * with gpe_batch_last_error, is that of the failing instance). */
 gpe_status gpe_batch_autotune(gpe_batch* batch, int iters);
 
-/* Last failure on batch ("" if none); NULL: the last failed gpe_batch_create. */
+/* Last failure on batch ("" if none); NULL: the last failed gpe_batch_create.
+ * The string is owned by the batch (or the library) and valid until the next
+ * call on it. */
 const char* gpe_batch_last_error(const gpe_batch* batch);
 
 /* Human-readable description of the last failure on ctx ("" if none).
