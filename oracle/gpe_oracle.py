@@ -328,6 +328,27 @@ class SolveOptions:
     cg: bool = True                # False: the projected gradient method (Algorithm 1)
 
 
+def conjugation_coefficient(prob, r, r_prev, Pr, rPr_prev, rule):
+    """beta_n of Section 5.3 (R7): "PR" is beta+ = max(beta_PR, 0) with
+    beta_PR = Re<r_n - r_{n-1}, P_n r_n> / <r_{n-1}, P_{n-1} r_{n-1}> (eq. CG:PR),
+    "FR" is <r_n, P_n r_n> / <r_{n-1}, P_{n-1} r_{n-1}> (eq. CG:FR)."""
+    if rule == "FR":
+        return inner(prob, r, Pr).real / rPr_prev
+    return max(inner(prob, r - r_prev, Pr).real / rPr_prev, 0.0)
+
+
+def is_descent_direction(prob, Hphi, p):
+    """Section 5.2: p is a descent direction iff Re<grad E(phi), p> = 2 Re<H_phi phi, p> < 0."""
+    return 2.0 * inner(prob, Hphi, p).real < 0.0
+
+
+def trial_step(m, curv, theta_default):
+    """theta_0 of eq. theta_opt under reading R4: the minimiser -Re<r,q> / (T2(q) - lambda)
+    of the second-order expansion when its curvature is positive (Re<r,q> = Re<H phi, q>
+    since Re<phi, q> = 0), else the default step of R5."""
+    return -m["R"] / curv if curv > 0.0 else theta_default
+
+
 def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterates=()):
     """Run PCG_C from phi0.  Returns (phi, report) where report['log'] holds one
     dict per iteration n (E_n, lambda_n, ||r_n||_inf, alpha_n, beta_n, theta_n,
@@ -364,23 +385,20 @@ def pcg_solve(prob: Problem, phi0, opts: SolveOptions | None = None, keep_iterat
         rPr = inner(prob, r, Pr).real
         if not opts.cg or n == 0 or rPr_prev is None:
             beta = 0.0
-        elif opts.beta == "FR":
-            beta = rPr / rPr_prev                                 # eq. CG:FR
         else:
-            beta = max(inner(prob, r - r_prev, Pr).real / rPr_prev, 0.0)  # eq. CG:PR, beta+
+            beta = conjugation_coefficient(prob, r, r_prev, Pr, rPr_prev, opts.beta)
         d = -Pr + beta * p_prev if beta != 0.0 else -Pr
         p = d - inner(prob, d, phi).real * phi             # projection M_phi d
         fallback = False
-        # Section 5.2: revert to the gradient step when Re<grad E, p> >= 0.
-        if 2.0 * inner(prob, Hphi, p).real >= 0.0:
+        # Section 5.2: revert to the gradient step when p is not a descent direction.
+        if not is_descent_direction(prob, Hphi, p):
             fallback = True
             beta = 0.0
             d = -Pr
             p = d - inner(prob, d, phi).real * phi
         q = p / norm(prob, p)
         m = step_moments(prob, phi, Hphi, lam, q)
-        curv = model_curvature(prob, phi, lam, q)
-        theta = -m["R"] / curv if curv > 0.0 else opts.theta_default  # eq. theta_opt
+        theta = trial_step(m, model_curvature(prob, phi, lam, q), opts.theta_default)
         if opts.line_search == "exact":
             theta = exact_step(m, prob.eta, theta)
         dE = delta_energy(m, prob.eta, theta)

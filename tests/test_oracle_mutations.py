@@ -32,6 +32,13 @@ QUICK_PINS = [
     P.test_P5_line_search_derivatives_match_differences,
     P.test_P5_exact_step_minimises_the_energy_along_the_geodesic,
     lambda: P.test_P14_interpolation_is_exact_for_band_limited_fields((16, 8), (32, 16)),
+    lambda: P.test_P13_thomas_fermi_mu_matches_the_continuum_closed_form_2d((1.0, 1.5)),
+    lambda: P.test_P15_lambda_tilde_closed_forms(100.0, 0.7),
+    P.test_P16_every_step_descends_and_beta_is_nonnegative,
+    P.test_P16_restart_and_fallback_take_the_preconditioned_gradient,
+    lambda: P.test_P16_polak_ribiere_directions_are_secant_conjugate("model"),
+    P.test_P16_trial_step_is_the_newton_step_of_the_energy_along_the_geodesic,
+    P.test_P16_conjugate_gradient_beats_the_gradient_method,
 ]
 
 
@@ -39,7 +46,7 @@ def pins_all_pass():
     for pin in QUICK_PINS:
         try:
             pin()
-        except AssertionError:
+        except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError):
             return False
     return True
 
@@ -176,7 +183,149 @@ def _interp_nyquist_unsplit(f, axis, Mf):
     return np.fft.ifft(G, axis=axis) * (Mf / Mc)
 
 
+# --- the shift lambda~ (eq. Opt_Alpha) and the scalar logic of Algorithm 2
+def _lt_half_eta(prob, phi):
+    kin = O.inner(prob, phi, -0.5 * O.laplacian(prob, phi)).real
+    pot = O.inner(prob, phi, prob.V * phi).real
+    return kin + pot + 0.5 * prob.eta * prob.weight * np.sum(np.abs(phi) ** 4)
+
+
+def _lt_with_rotation(prob, phi):
+    return O.chemical_potential(prob, phi)
+
+
+def _beta_without_max(prob, r, r_prev, Pr, rPr_prev, rule):
+    return O.inner(prob, r - r_prev, Pr).real / rPr_prev
+
+
+def _beta_r_n_numerator(prob, r, r_prev, Pr, rPr_prev, rule):
+    return max(O.inner(prob, r, Pr).real / rPr_prev, 0.0)
+
+
+def _theta_half_curvature(m, curv, theta_default):
+    return -m["R"] / (0.5 * curv) if curv > 0.0 else theta_default
+
+
+def _never_fallback(prob, Hphi, p):
+    return True
+
+
+def _fallback_inverted(prob, Hphi, p):
+    return 2.0 * O.inner(prob, Hphi, p).real >= 0.0
+
+
+# --- further single-function mistakes, one per remaining oracle function
+_orig_dft = O.dft_axis
+_orig_coord = O.Problem.coord
+
+
+def _dft_inverse_unscaled(prob, f, i, inverse=False):
+    g = _orig_dft(prob, f, i, inverse)
+    return g * f.shape[prob.axis(i)] if inverse else g
+
+
+def _coord_shifted(self, i):
+    return _orig_coord(self, i) + self.h[i]
+
+
+def _laplacian_one_axis(prob, f):
+    return O.d2_axis(prob, f, 0)
+
+
+def _A_without_V(prob, f):
+    return -0.5 * O.laplacian(prob, f) - prob.omega * O.Lz(prob, f)
+
+
+def _energy_full_interaction(prob, phi):
+    kin = O.inner(prob, phi, -0.5 * O.laplacian(prob, phi)).real
+    pot = O.inner(prob, phi, prob.V * phi).real
+    inter = prob.eta * prob.weight * np.sum(np.abs(phi) ** 4)
+    rot = O.inner(prob, phi, -prob.omega * O.Lz(prob, phi)).real
+    return dict(kin=kin, pot=pot, int=inter, rot=rot, total=kin + pot + inter + rot)
+
+
+def _lambda_linear_part(prob, phi):
+    return O.inner(prob, phi, O.apply_A(prob, phi)).real
+
+
+def _kinetic_symbol_no_half(prob):
+    return sum(prob.freq(i) ** 2 for i in range(prob.dim))
+
+
+def _pv_without_eta(prob, phi, alpha):
+    return 1.0 / (alpha + prob.V)
+
+
+_orig_moments = O.step_moments
+
+
+def _moments_R_sign(prob, phi, Hphi, lam, q):
+    m = _orig_moments(prob, phi, Hphi, lam, q)
+    m["R"] = -m["R"]
+    return m
+
+
+def _exact_step_is_model_step(m, eta, theta0, iters=30):
+    return theta0
+
+
+def _tf_mu_half_eta(prob, iters=200):
+    V, w, eta = prob.V, prob.weight, 0.5 * prob.eta
+    lo, hi = float(V.min()), float(V.max()) + eta / (w * V.size)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if w * np.sum(np.maximum(mid - V, 0.0)) / eta < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def _interpolate_axes_swapped(prob_c, phi_c, prob_f):
+    g = phi_c
+    for i in range(prob_c.dim):
+        g = O.interpolate_axis(g, i, prob_f.n[i])
+    return g
+
+
+def _project_nothing(prob, phi, h):
+    return h.copy()
+
+
+_orig_tsolve = O.tangent_solve
+
+
+def _tangent_solve_half(prob, phi, lam, rhs, tol=1e-12, max_iter=5000, alpha=None):
+    z, it, res = _orig_tsolve(prob, phi, lam, rhs, tol, max_iter, alpha)
+    return 0.5 * z, it, res
+
+
+def _density_loss_unweighted(prob, phi, rho):
+    return np.sum((np.abs(phi) ** 2 - rho) ** 2)
+
+
 MUTATIONS = {
+    "lt_half_eta": ("lambda_tilde", _lt_half_eta),
+    "lt_with_rotation": ("lambda_tilde", _lt_with_rotation),
+    "beta_without_max": ("conjugation_coefficient", _beta_without_max),
+    "beta_r_n_numerator": ("conjugation_coefficient", _beta_r_n_numerator),
+    "theta_half_curvature": ("trial_step", _theta_half_curvature),
+    "never_fallback": ("is_descent_direction", _never_fallback),
+    "fallback_inverted": ("is_descent_direction", _fallback_inverted),
+    "dft_inverse_unscaled": ("dft_axis", _dft_inverse_unscaled),
+    "laplacian_one_axis": ("laplacian", _laplacian_one_axis),
+    "A_without_V": ("apply_A", _A_without_V),
+    "energy_full_interaction": ("energy_parts", _energy_full_interaction),
+    "lambda_linear_part": ("chemical_potential", _lambda_linear_part),
+    "kinetic_symbol_no_half": ("kinetic_symbol", _kinetic_symbol_no_half),
+    "pv_without_eta": ("precond_V", _pv_without_eta),
+    "moments_R_sign": ("step_moments", _moments_R_sign),
+    "exact_step_is_model_step": ("exact_step", _exact_step_is_model_step),
+    "tf_mu_half_eta": ("thomas_fermi_mu", _tf_mu_half_eta),
+    "interpolate_axes_swapped": ("interpolate", _interpolate_axes_swapped),
+    "project_nothing": ("tangent_project", _project_nothing),
+    "tangent_solve_half": ("tangent_solve", _tangent_solve_half),
+    "density_loss_unweighted": ("density_loss", _density_loss_unweighted),
     "Lz_sign": ("Lz", _lz_wrong_sign),
     "Lz_axes": ("Lz", _lz_swapped_axes),
     "no_weight": ("inner", _inner_unweighted),
@@ -209,9 +358,11 @@ def test_mutation_is_caught(case):
         assert not pins_all_pass(), f"planted mistake {case} passed every pin"
 
 
-def test_frequency_scale_mutation_is_caught():
-    O.Problem.freq = _freq_twice
+@pytest.mark.parametrize("attr,fn", [("freq", _freq_twice), ("coord", _coord_shifted)])
+def test_problem_method_mutation_is_caught(attr, fn):
+    orig = getattr(O.Problem, attr)
+    setattr(O.Problem, attr, fn)
     try:
         assert not pins_all_pass()
     finally:
-        O.Problem.freq = _orig_freq
+        setattr(O.Problem, attr, orig)

@@ -6,7 +6,15 @@ P2 sign/scale of L_z via phi_b; P3 Hermiticity; P4 gradient = 2 H phi (FD);
 P5 exact energy change along the geodesic and its curvature (FD);
 P6 preconditioner symmetry/positivity and exact inversion of P_Delta;
 P7 converged energies printed in the paper's Table 2;
-P8 method invariants (monotone energy, unit norm); P9 stationarity.
+P8 method invariants (monotone energy, unit norm); P9 stationarity;
+P10-P12 derivatives (differences of energies and of re-solved ground states);
+P13 Thomas-Fermi mu (continuum closed forms); P14 spectral interpolation
+(band-limited exactness, brute-force trigonometric sums);
+P15 the shift lambda~ of eq. Opt_Alpha (closed forms of the harmonic states);
+P16 the scalar logic of Algorithm 2: every step descends and beta+ >= 0,
+restarts take the preconditioned gradient, Polak-Ribiere directions are
+secant-conjugate (Hestenes-Stiefel), theta_0 is the Newton step of the energy
+along the geodesic, and CG needs fewer iterations than the gradient method.
 """
 import json
 import os
@@ -553,3 +561,163 @@ def test_P14_interpolation_keeps_coarse_values_and_matches_the_trigonometric_sum
                     tot += w * Fp * np.exp(1j * (px * np.pi / L[0] * (x + L[0]) + py * np.pi / L[1] * (y + L[1])))
             tot /= nc[0] * nc[1]
             assert abs(tot - got[j, i]) < 1e-12, (i, j)
+
+
+# ---------------------------------------------------------------- P15: the shift alpha = lambda~
+@pytest.mark.parametrize("eta,omega", [(0.0, 0.0), (0.0, 0.7), (100.0, 0.0), (100.0, 0.7)])
+def test_P15_lambda_tilde_closed_forms(eta, omega):
+    """lambda~(phi) = int 1/2|grad phi|^2 + V|phi|^2 + eta|phi|^4 (eq. Opt_Alpha) for
+    V = r^2/2 and the two lowest harmonic states (Section 6, initial data (a), (b)):
+    phi_a = pi^{-1/2} e^{-r^2/2} has kinetic + potential energy 1 and int |phi_a|^4 = 1/(2 pi);
+    phi_b = (x+iy) phi_a has 2 and int |phi_b|^4 = 1/(4 pi).  lambda~ carries no
+    rotation term, so it is independent of omega, and lambda~ - lambda = omega <phi, L_z phi>,
+    which is omega for phi_b (L_z phi_b = phi_b) and 0 for the radial phi_a."""
+    n, L = (64, 64), (8.0, 8.0)
+    p = O.Problem(n, L, eta, omega, I.harmonic(n, L))
+    a, b = I.phi_a(n, L), I.phi_b(n, L)
+    assert abs(O.norm(p, b) - 1.0) < 1e-13
+    assert abs(O.lambda_tilde(p, a) - (1.0 + eta / (2.0 * np.pi))) < 1e-12
+    assert abs(O.lambda_tilde(p, b) - (2.0 + eta / (4.0 * np.pi))) < 1e-12
+    assert abs(O.lambda_tilde(p, b) - O.chemical_potential(p, b) - omega) < 1e-12
+    assert abs(O.lambda_tilde(p, a) - O.chemical_potential(p, a)) < 1e-12
+
+
+# ---------------------------------------------------------------- P16: the scalar logic of Algorithm 2
+def _solve_with_iterates(p, phi0, n_iter, **kw):
+    opts = O.SolveOptions(tol_res_inf=1e-8, max_iter=n_iter, **kw)
+    _, rep = O.pcg_solve(p, phi0, opts, keep_iterates=tuple(range(n_iter + 1)))
+    return rep
+
+
+def _directions(p, rep):
+    """Per accepted iteration n: phi_n, the residual r_n = H phi_n - lambda_n phi_n from
+    the Hamiltonian (pinned by P1-P4), and the unit search direction q_n recovered from the
+    retraction phi_{n+1} = cos(theta_n) phi_n + sin(theta_n) q_n (which has unit norm
+    because Re<phi_n, q_n> = 0): nothing here repeats the solver's scalar formulas."""
+    out = []
+    its, log = rep["iterates"], rep["log"]
+    for n in range(rep["iters"]):
+        if n + 1 not in its:
+            break
+        phi, th = its[n], log[n]["theta"]
+        Hphi = O.apply_H(p, phi, phi)
+        r = Hphi - O.inner(p, phi, Hphi).real * phi
+        q = (its[n + 1] - np.cos(th) * phi) / np.sin(th)
+        out.append(dict(n=n, phi=phi, r=r, q=q, **{k: log[n][k] for k in ("theta", "beta", "fallback", "backtracks")}))
+    return out
+
+
+def _fast_rotation_32():
+    """A small fast-rotation problem whose first 40 iterations include a Polak-Ribiere
+    restart (beta_PR < 0, iteration 6) and a descent-check fallback (iteration 16)."""
+    n, L = (32, 32), (6.0, 6.0)
+    p = O.Problem(n, L, 200.0, 0.95, I.harmonic(n, L))
+    return p, I.perturbed(I.phi_d(n, L, 0.95), 3, n, L)
+
+
+def _cosine(p, f, g):
+    return O.inner(p, f, g).real / (O.norm(p, f) * O.norm(p, g))
+
+
+def test_P16_every_step_descends_and_beta_is_nonnegative():
+    """Section 5.2 enforces a descent direction at every step (reverting to the
+    gradient step otherwise), so Re<grad E(phi_n), q_n> = 2 Re<r_n, q_n> < 0 for
+    every accepted q_n; the energy decreases at every step; beta+ = max(beta_PR, 0)
+    of eq. CG:PR is never negative."""
+    p, phi0 = _fast_rotation_32()
+    rep = _solve_with_iterates(p, phi0, 40)
+    dirs = _directions(p, rep)
+    assert len(dirs) == 40
+    assert sum(d["fallback"] for d in dirs) >= 1
+    assert any(d["n"] > 0 and d["beta"] == 0.0 and not d["fallback"] for d in dirs)  # a PR restart happened
+    for d in dirs:
+        assert O.inner(p, d["r"], d["q"]).real < 0.0, d["n"]
+        assert d["beta"] >= 0.0, d["n"]
+    E = [e["E"] for e in rep["log"]]
+    assert all(b < a for a, b in zip(E, E[1:]))
+
+
+def test_P16_restart_and_fallback_take_the_preconditioned_gradient():
+    """When beta = 0 (first step, PR restart, or the descent-check fallback) the step is
+    the projected preconditioned gradient, p = -(P r - Re<P r, phi> phi) with P = P_C and
+    alpha = lambda~ (pinned by P6, P15); with beta > 0 the direction differs from it."""
+    p, phi0 = _fast_rotation_32()
+    rep = _solve_with_iterates(p, phi0, 40)
+    n_gradient = 0
+    for d in _directions(p, rep):
+        phi = d["phi"]
+        Pr = O.precond_C(p, phi, d["r"], O.lambda_tilde(p, phi))
+        g = -(Pr - O.inner(p, Pr, phi).real * phi)
+        c = _cosine(p, g, d["q"])
+        if d["beta"] == 0.0:
+            n_gradient += 1
+            assert c > 1.0 - 1e-10, (d["n"], c)
+        else:
+            assert c < 1.0 - 1e-6, (d["n"], c)
+    assert n_gradient >= 3
+
+
+@pytest.mark.parametrize("line_search", ["model", "exact"])
+def test_P16_polak_ribiere_directions_are_secant_conjugate(line_search):
+    """With (near-)exact line searches the Polak-Ribiere coefficient equals the
+    Hestenes-Stiefel one, whose defining property is that the new direction is
+    orthogonal to the change of gradient, Re<r_n - r_{n-1}, d_n> = 0 (the linear-case
+    equivalence the paper states under eq. CG:FR).  On the sphere this holds up to
+    O(theta) terms, so once the steps are small |cos(r_n - r_{n-1}, q_n)| is small,
+    whereas for example the Fletcher-Reeves rule leaves it of order 0.1-0.5 here."""
+    w = I.workload("c64_2d")
+    p = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    rep = _solve_with_iterates(p, w["phi0"], 60, line_search=line_search)
+    assert rep["status"] == "converged"
+    dirs = _directions(p, rep)
+    checked = 0
+    for prev, d in zip(dirs, dirs[1:]):
+        if prev["theta"] < 1e-3 and d["beta"] > 0.0 and not d["fallback"]:
+            y = d["r"] - prev["r"]
+            assert abs(_cosine(p, y, d["q"])) < 1e-2, (d["n"], _cosine(p, y, d["q"]))
+            checked += 1
+    assert checked >= 15
+
+
+def test_P16_trial_step_is_the_newton_step_of_the_energy_along_the_geodesic():
+    """eq. theta_opt: theta_0 minimises the second-order expansion of
+    t -> E(cos t phi_n + sin t q_n), i.e. theta_0 = -E'(0) / E''(0), taken here by
+    central differences of the energy (P5 pins the expansion).  Section 5.2 reports
+    that near a minimum this step always decreases the energy, so no backtracking
+    happens once the residual is small."""
+    w = I.workload("c64_2d")
+    p = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    rep = _solve_with_iterates(p, w["phi0"], 60)
+    assert rep["status"] == "converged"
+    checked = 0
+    for d in _directions(p, rep):
+        res = rep["log"][d["n"]]["res_inf"]
+        if res < 1e-3:
+            assert d["backtracks"] == 0, d["n"]
+        if d["backtracks"] or not (1e-5 < d["theta"] < 0.3):
+            continue
+        phi, q = d["phi"], d["q"]
+        Et = lambda t: O.energy(p, np.cos(t) * phi + np.sin(t) * q)  # noqa: E731
+        # central differences with one Richardson step (errors O(h^4)); h = 1e-3 keeps
+        # the cancellation in E(h) - 2E(0) + E(-h) below 1e-9 relative
+        E0, h = Et(0.0), 1e-3
+        Ep = {k: Et(k * h) for k in (-2, -1, 1, 2)}
+        e1 = (8 * (Ep[1] - Ep[-1]) - (Ep[2] - Ep[-2])) / (12 * h)
+        e2 = (16 * (Ep[1] + Ep[-1]) - (Ep[2] + Ep[-2]) - 30 * E0) / (12 * h * h)
+        assert e2 > 0
+        assert abs(d["theta"] + e1 / e2) < 1e-5 * d["theta"], (d["n"], d["theta"], -e1 / e2)
+        checked += 1
+    assert checked >= 5
+
+
+def test_P16_conjugate_gradient_beats_the_gradient_method():
+    """Section 6 reports that PCG_C needs far fewer iterations than PG_C (the projected
+    gradient method of Algorithm 1 with the same preconditioner and step rule) on the
+    2D rotating problems; both reach the same ground state."""
+    w = I.workload("c64_2d")
+    p = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
+    _, cg = O.pcg_solve(p, w["phi0"], O.SolveOptions(tol_res_inf=1e-8, max_iter=1000))
+    _, pg = O.pcg_solve(p, w["phi0"], O.SolveOptions(tol_res_inf=1e-8, max_iter=1000, cg=False))
+    assert cg["status"] == "converged" and pg["status"] == "converged"
+    assert abs(cg["E"] - pg["E"]) < 1e-10 * abs(cg["E"])
+    assert 2 * cg["iters"] < pg["iters"]
