@@ -98,6 +98,9 @@ typedef struct {
   int precond;          /* [GPE_PRECOND_C] preconditioner of Section 5.4 (below) */
   int beta_rule;        /* [GPE_BETA_PR] conjugation coefficient (below) */
   int line_search;      /* [GPE_LINE_MODEL] step size (below) */
+  int wait_polls;       /* use_graph = 2: polls (>= 32 ns apart) of each grid-barrier wait before the
+                         * persistent kernel gives up, leaves its loop and the solve returns
+                         * GPE_ERR_TIMEOUT with the context still usable; 0 = 2^26 (seconds) [0] */
 } gpe_solve_opts;
 
 /* gpe_solve_opts.precond, with alpha = lambda~_n (eq. Opt_Alpha) in every case:
@@ -326,11 +329,13 @@ gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* op
  * library that promised never to call the allocator, or with the device
  * memory already exhausted -- and so cannot create a context.
  *
- * Computes the same out = H_phi f as gpe_apply_H, with the same kernels, but
- * takes the problem directly and keeps its intermediate field, grid tables,
- * reduction partials and control block in one fixed static device array of
- * libgpe (about 17 MiB, held by every GPU that loads the library until the
- * process exits).  It calls no cudaMalloc/cudaFree and no allocating library.
+ * Computes the same out = H_phi f as gpe_apply_H with the same pass kernels,
+ * under default plans (a context's tuned plans may sum in another order, so
+ * results agree to rounding), but takes the problem directly and keeps its
+ * intermediate field, grid tables, reduction partials and control block in
+ * one fixed static device array of libgpe (about 17 MiB, held by every GPU
+ * that loads the library until the process exits).  It calls no
+ * cudaMalloc/cudaFree and no allocating library.
  *  prob    : as for gpe_create; prob->prec selects the element types.
  *  V_dev   : real potential on the device, float64 for GPE_FP64, float32 for
  *            GPE_MIXED, [z][y][x].
@@ -338,14 +343,18 @@ gpe_status gpe_pcg_solve(gpe_ctx* ctx, void* phi_inout, const gpe_solve_opts* op
  *            complex64 (GPE_MIXED); out may alias f.
  *  stream  : cudaStream_t ordering the work (NULL = legacy default stream).
  *  err, err_len : optional buffer for a message (NUL-terminated), may be NULL.
- * Limit: N * sizeof(element) <= 16 MiB, i.e. at most 2^20 complex128 or 2^21
- * complex64 points; larger grids return GPE_ERR_UNSUPPORTED with the sizes in
- * err.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call reuses the same array and leaves its last contents there, so
- * calls whose GPU work can overlap (other streams, other host threads) race:
- * serialise them.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED,
- * GPE_ERR_CUDA. */
+ * Limits: N * sizeof(element) <= 16 MiB, i.e. at most 2^20 complex128 or 2^21
+ * complex64 points; and at most 8192 thread blocks in any axis's pass (the
+ * partials the array holds), which excludes some flat 3D grids such as
+ * 512 x 8 x 512.  Both are checked before any work is queued: such calls
+ * return GPE_ERR_UNSUPPORTED with the sizes in err and leave out untouched.
+ * Each call outside a stream capture looks up the array's device address on
+ * the current device (cudaGetSymbolAddress); a call inside a capture uses the
+ * address of the last uncaptured call on that device, so make one call on
+ * each device before capturing.  Every call reuses the same array and leaves
+ * its last contents there, so calls whose GPU work can overlap (other
+ * streams, other host threads) race: serialise them.  Asynchronous.  Errors:
+ * GPE_ERR_ARG, GPE_ERR_UNSUPPORTED, GPE_ERR_CUDA. */
 gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V_dev, const void* phi_dev, const void* f_dev,
                                void* out_dev, void* stream, char* err, size_t err_len);
 
@@ -438,6 +447,20 @@ gpe_status gpe_batch_autotune(gpe_batch* batch, int iters);
  * The string is owned by the batch (or the library) and valid until the next
  * call on it. */
 const char* gpe_batch_last_error(const gpe_batch* batch);
+
+/* ---- Measurement ---------------------------------------------------------
+ * Arithmetic-pipe rate of the current device, the roof of the kernels that
+ * memory does not bound (FP64 passes: FP64 pipe; double-single and
+ * single-precision transforms: FP32 pipe).  Not part of the method (the paper
+ * has no counterpart): independent fused multiply-add chains in registers,
+ * 8 blocks of 256 threads per SM, best of 3 CUDA-event-timed launches after a
+ * warm-up, at the clocks of the moment.
+ *  kind   : 0 FP64 fma, 1 FP32 fma, 2 packed two-wide FP32 fma (fma.rn.f32x2).
+ *  stream : cudaStream_t (NULL = legacy default stream); synchronised.
+ *  gflops : out, 10^9 floating-point operations per second (an FMA is 2).
+ * Allocates and frees a small result buffer.  Errors: GPE_ERR_ARG (kind
+ * outside 0..2, NULL gflops), GPE_ERR_CUDA. */
+gpe_status gpe_alu_peak(int kind, void* stream, double* gflops);
 
 /* Human-readable description of the last failure on ctx ("" if none).
  * The string is owned by ctx and valid until its next call. ctx NULL gives

@@ -1,6 +1,6 @@
 """Operator microbenchmark: times one libgpe entry point on a synthetic field.
 
-    python -m paper_1611_02045_gb300.opbench --grid 256 256 512 --prec mixed --op apply_H --iters 20
+    python opbench.py --grid 256 256 512 --prec mixed --op apply_H --iters 20
 
 Prints one JSON line: median CUDA-event time per call, points, and the
 effective bandwidth for the given algorithmic bytes per point.  Also used as

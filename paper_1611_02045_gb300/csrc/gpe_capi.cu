@@ -294,6 +294,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->precond = GPE_PRECOND_C;
   o->beta_rule = GPE_BETA_PR;
   o->line_search = GPE_LINE_MODEL;
+  o->wait_polls = 0;
   return GPE_OK;
 }
 
@@ -793,7 +794,7 @@ static cudaError_t launch_persist(int mode, int M, int dim, const PersistArgs& P
 
 // Launch the persistent solve for one phase.  *launched = false when the
 // kernel cannot be made co-resident (the caller falls back to the graph).
-static gpe_status run_persistent(gpe_ctx* c, int mode, bool* launched) {
+static gpe_status run_persistent(gpe_ctx* c, int mode, bool* launched, int wait_polls) {
   *launched = false;
   const int M = c->n[0];
   const int Tl = M / 8;
@@ -831,6 +832,7 @@ static gpe_status run_persistent(gpe_ctx* c, int mode, bool* launched) {
   P.bar = c->pers_bar;
   P.err = reinterpret_cast<int*>(c->pers_bar + 2);
   P.units = units;
+  P.spin_limit = wait_polls > 0 ? (long long)wait_polls : kSpinLimit;
   // dynamic shared memory: the larger of an x unit and a y/z unit, in the
   // widest transform type of this mode
   const size_t csz = (mode == 0) ? 8 : 16;
@@ -925,7 +927,7 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
     }
   }
   if (!done_launch && o.use_graph == 2 && persist_eligible(c)) {
-    s = run_persistent(c, mode, &done_launch);
+    s = run_persistent(c, mode, &done_launch, o.wait_polls);
     if (s != GPE_OK) return s;
     if (done_launch) loop = 2;
   }
@@ -949,7 +951,14 @@ static gpe_status run_phase(gpe_ctx* c, int mode, Ctl& h, const gpe_solve_opts& 
     }
   }
   GPE_CU(c, cudaMemcpyAsync(&h, c->ctl_solve, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+  int wait_failed = 0;
+  if (loop == 2)  // a barrier wait of the persistent kernel gave up (any block)
+    GPE_CU(c, cudaMemcpyAsync(&wait_failed, c->pers_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   GPE_CU(c, cudaStreamSynchronize(c->st));
+  if (wait_failed) {
+    h.status = GPE_ERR_TIMEOUT;
+    h.done = 1;
+  }
   return GPE_OK;
 }
 
@@ -975,7 +984,8 @@ static Ctl solve_ctl(const gpe_ctx* c, const gpe_solve_opts& o, int log_cap) {
 
 static gpe_status check_opts(gpe_solve_opts& o, std::string& err) {
   if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.tol_res_inf >= 0.0) || o.stall_window < 1 || o.precond < 0 ||
-      o.precond > 5 || o.beta_rule < 0 || o.beta_rule > 1 || o.line_search < 0 || o.line_search > 1) {
+      o.precond > 5 || o.beta_rule < 0 || o.beta_rule > 1 || o.line_search < 0 || o.line_search > 1 ||
+      o.wait_polls < 0) {
     err = "invalid solve options";
     return GPE_ERR_ARG;
   }

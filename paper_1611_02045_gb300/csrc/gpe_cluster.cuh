@@ -297,15 +297,16 @@ cudaError_t launch_cluster_apply_H_one(const ClusterHArgs& a, cudaStream_t st) {
   const int threads = (M / EV) * R;
   const size_t smem = ClusterHSmem<T, M>::bytes;
   auto kern = cluster_apply_H<T, M, EV>;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce attr;
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (csize > 8) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
-    attr = true;
+    attr.set(dev);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nbatch * csize));
@@ -334,7 +335,9 @@ cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st
   const int threads = (M / EV) * R;
   const size_t smem = (size_t)(2 * R * M + R * (M + M / 16)) * sizeof(cplx<T>);
   auto kern = cluster_apply_H_stream<T, M, EV, RR>;
-  static int max_clusters = -1;
+  static std::atomic<int> max_clusters_dev[64];  // per device; 0 = not yet queried
+  const int dev = DeviceOnce::device();
+  int max_clusters = (dev >= 0 && dev < 64) ? max_clusters_dev[dev].load() : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
@@ -346,7 +349,7 @@ cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (max_clusters < 0) {
+  if (max_clusters <= 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (csize > 8) {
@@ -358,6 +361,7 @@ cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st
     e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
     if (e != cudaSuccess || n < 1) { cudaGetLastError(); n = 1; }
     max_clusters = n;
+    if (dev >= 0 && dev < 64) max_clusters_dev[dev].store(n);
   }
   const int ncl = a.nbatch < max_clusters ? a.nbatch : max_clusters;
   cfg.gridDim = dim3((unsigned)(ncl * csize));

@@ -257,11 +257,12 @@ constexpr size_t cluster_solve_smem() {
 }
 
 // Kernel attributes (dynamic shared memory, non-portable cluster size), set
-// once; call before any stream capture that launches the kernel.
+// once per device; call before any stream capture that launches the kernel.
 template <int M>
 cudaError_t cluster_solve_attrs() {
-  static bool attr = false;
-  if (attr) return cudaSuccess;
+  static DeviceOnce attr;
+  const int dev = DeviceOnce::device();
+  if (attr.done(dev)) return cudaSuccess;
   auto kern = cluster_solve<M>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_solve_smem<M>());
   if (e != cudaSuccess) return e;
@@ -269,7 +270,7 @@ cudaError_t cluster_solve_attrs() {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  attr = true;
+  attr.set(dev);
   return cudaSuccess;
 }
 

@@ -4,7 +4,25 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace gpe {
+
+// Per-device "done once" flag for kernel attribute set-up
+// (cudaFuncSetAttribute applies to the current device's context only).
+// Thread-safe; devices 0..63 (others redo the set-up on every launch, which is
+// correct, only slower).  Setting an attribute twice is harmless.
+struct DeviceOnce {
+  std::atomic<unsigned long long> bits{0};
+  static int device() {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+  }
+  bool done(int dev) const { return dev >= 0 && dev < 64 && ((bits.load(std::memory_order_acquire) >> dev) & 1ull); }
+  void set(int dev) {
+    if (dev >= 0 && dev < 64) bits.fetch_or(1ull << dev, std::memory_order_release);
+  }
+};
 
 // Number of doubles in one per-iteration log row (matches GPE_LOG_FIELDS).
 constexpr int kLogFields = 12;

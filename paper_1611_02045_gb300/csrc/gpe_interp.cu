@@ -66,11 +66,12 @@ cudaError_t launch_interp_one(const InterpArgs& a, cudaStream_t st) {
   if (lpb < 1) lpb = 1;
   while (lpb > 1 && a.lines % lpb != 0) lpb >>= 1;
   const size_t smem = (size_t)lpb * LS * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce attr;
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
     const cudaError_t e = cudaFuncSetAttribute(k_interp<Mc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.set(dev);
   }
   k_interp<Mc><<<(unsigned)(a.lines / lpb), (unsigned)(Tl * lpb), smem, st>>>(a);
   return cudaGetLastError();

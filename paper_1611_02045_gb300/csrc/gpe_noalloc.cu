@@ -112,21 +112,52 @@ extern "C" gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V
     return GPE_ERR_UNSUPPORTED;
   }
 
-  // Pass plans: the same rules as a context's, with the FP64 thread cap.
+  // Pass plans for every axis, checked before anything is queued: the same
+  // rules as a context's default plans, with the FP64 thread cap.
   const int maxT = 256;
   int lpb = maxT / (n[0] / 8);
   if (lpb < 1) lpb = 1;
   const long long nlines = (long long)n[1] * (prob->dim == 3 ? n[2] : 1);
   while (lpb > 1 && (lpb > nlines || nlines / lpb < kTargetBlocks)) lpb >>= 1;
-  const int nblocks_x = (int)(nlines / lpb);
-  if (nblocks_x > kMaxBlocks) { set_err(err, err_len, "too many thread blocks for the scratch partials"); return GPE_ERR_UNSUPPORTED; }
+  int tx_ax[3] = {0, 0, 0};
+  long long blocks_ax[3] = {nlines / lpb, 0, 0};
+  for (int ax = 1; ax < prob->dim; ++ax) {
+    const int nx = n[0];
+    const long long outer = (ax == 1) ? (prob->dim == 3 ? n[2] : 1) : n[1];
+    int tx = 16 < nx ? 16 : nx;
+    while (tx > 1 && tx * (n[ax] / 8) > maxT) tx >>= 1;
+    while (tx > 4 && (long long)(nx / tx) * outer < kTargetBlocks) tx >>= 1;
+    tx_ax[ax] = tx;
+    blocks_ax[ax] = (long long)(nx / tx) * outer;
+  }
+  for (int ax = 0; ax < prob->dim; ++ax) {
+    if (blocks_ax[ax] > kMaxBlocks) {
+      char msg[160];
+      std::snprintf(msg, sizeof(msg), "axis %d needs %lld thread blocks; the scratch holds reduction partials for "
+                    "at most %d", ax, blocks_ax[ax], kMaxBlocks);
+      set_err(err, err_len, msg);
+      return GPE_ERR_UNSUPPORTED;
+    }
+  }
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) { set_err(err, err_len, "no usable CUDA device"); return GPE_ERR_CUDA; }
-  // One-time set-up per device (this device is current): the device address
-  // of the scratch symbol.
-  if (!g_scratch_addr[dev]) {
+  cudaStream_t st = (cudaStream_t)stream;
+  // The device address of the scratch symbol on this device (current).  It is
+  // looked up again on every call outside a stream capture, so a module
+  // reloaded after cudaDeviceReset is followed; inside a capture the address
+  // from the last uncaptured call on this device is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;  // treat as capturing: no driver call that capture forbids
+  }
+  if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone) {
+      set_err(err, err_len, "first call on this device inside a stream capture: call once before capturing");
+      return GPE_ERR_CUDA;
+    }
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -136,7 +167,6 @@ extern "C" gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V
     g_scratch_addr[dev] = ptr;
   }
   unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
-  cudaStream_t st = (cudaStream_t)stream;
 
   // The reduction ticket must start at zero; the other contents are fully
   // rewritten before they are read.
@@ -172,18 +202,13 @@ extern "C" gpe_status gpe_apply_H_noalloc(const gpe_problem* prob, const void* V
     a.ticket = reinterpret_cast<unsigned*>(base + kTicketOff);
     if (ax == 0) {
       a.lpb = lpb;
-      a.nblocks = nblocks_x;
+      a.nblocks = (int)blocks_ax[0];
       e = launch_pass(mode, P_HX, a, st);
     } else {
       const int nx = n[0];
-      const long long outer = (ax == 1) ? (prob->dim == 3 ? n[2] : 1) : n[1];
-      int tx = 16 < nx ? 16 : nx;
-      while (tx > 1 && tx * (n[ax] / 8) > maxT) tx >>= 1;
-      while (tx > 4 && (long long)(nx / tx) * outer < kTargetBlocks) tx >>= 1;
-      a.tx = tx;
-      a.ntx = nx / tx;
-      a.nblocks = (int)((long long)a.ntx * outer);
-      if (a.nblocks > kMaxBlocks) { set_err(err, err_len, "too many thread blocks for the scratch partials"); return GPE_ERR_UNSUPPORTED; }
+      a.tx = tx_ax[ax];
+      a.ntx = nx / a.tx;
+      a.nblocks = (int)blocks_ax[ax];
       a.stride = (ax == 1) ? nx : (long long)nx * n[1];
       a.outer_stride = (ax == 1) ? (long long)nx * n[1] : nx;
       a.last_axis = (ax == prob->dim - 1);

@@ -879,11 +879,12 @@ cudaError_t launch_one(const PassArgs& a, cudaStream_t st) {
   void (*kern)(PassArgs);
   if constexpr (contig) kern = pass_x<TF, typename MT::TS, typename MT::TD, M, ROLE, EV>;
   else kern = pass_s<TF, M, ROLE, EV>;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static DeviceOnce attr;
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr.set(dev);
   }
   kern<<<a.nblocks, threads, smem, st>>>(a);
   return cudaGetLastError();

@@ -26,6 +26,7 @@ struct PersistArgs {
   unsigned* bar;     // [0] arrivals, [1] generation (zero before launch)
   int* err;          // 1 when a barrier wait gave up (zero before launch)
   long long units;   // work units per pass (equal for every pass: square/cubic grids)
+  long long spin_limit;  // polls of one barrier wait before it gives up (kSpinLimit by default)
 };
 
 // ~2^26 polls of >= 32 ns: seconds, far beyond any legitimate wait.
@@ -46,7 +47,8 @@ __device__ __forceinline__ bool grid_sync(const PersistArgs& P) {
     } else {
       long long spins = 0;
       while (*gen == g) {
-        if (++spins > kSpinLimit) {
+        // give up after spin_limit polls, or at once when another block already gave up
+        if (++spins > P.spin_limit || *(volatile int*)P.err) {
           ok = 0;
           atomicExch(P.err, 1);
           break;

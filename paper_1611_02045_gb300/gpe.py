@@ -39,7 +39,7 @@ class gpe_solve_opts(C.Structure):
                 ("theta_default", C.c_double), ("max_backtracks", C.c_int), ("cg", C.c_int),
                 ("stall_window", C.c_int), ("switch_res", C.c_double), ("max_iter_lo", C.c_int),
                 ("use_graph", C.c_int), ("refine_restart", C.c_int), ("precond", C.c_int),
-                ("beta_rule", C.c_int), ("line_search", C.c_int)]
+                ("beta_rule", C.c_int), ("line_search", C.c_int), ("wait_polls", C.c_int)]
 
 
 class gpe_report(C.Structure):
@@ -65,7 +65,7 @@ EXPORTED = ("gpe_solve_opts_default", "gpe_create", "gpe_destroy", "gpe_apply_H"
             "gpe_energy", "gpe_set_problem", "gpe_energy_grad", "gpe_tangent_solve", "gpe_density_adjoint",
             "gpe_pcg_solve", "gpe_last_error", "gpe_batch_create", "gpe_batch_solve", "gpe_batch_destroy",
             "gpe_batch_last_error", "gpe_autotune", "gpe_set_plan", "gpe_get_plan", "gpe_batch_autotune",
-            "gpe_thomas_fermi", "gpe_interpolate")
+            "gpe_thomas_fermi", "gpe_interpolate", "gpe_alu_peak")
 MODE_NAMES = ("complex64", "fp64", "refinement")
 _STRING_RETURNING = ("gpe_last_error", "gpe_batch_last_error")
 
@@ -105,6 +105,7 @@ def lib():
         L.gpe_batch_autotune.argtypes = [vp, C.c_int]
         L.gpe_thomas_fermi.argtypes = [vp, vp, C.POINTER(C.c_double)]
         L.gpe_interpolate.argtypes = [vp, vp, vp, vp]
+        L.gpe_alu_peak.argtypes = [C.c_int, vp, C.POINTER(C.c_double)]
         for name in EXPORTED:
             if name not in _STRING_RETURNING:
                 getattr(L, name).restype = C.c_int
@@ -127,6 +128,18 @@ def _addr(x):
             raise ValueError("field arrays must be C-contiguous")
         return x.ctypes.data
     raise TypeError(f"unsupported field type {type(x)}")
+
+
+ALU_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp32x2_fma": 2}
+
+
+def alu_peak(kind, stream=None):
+    """gpe_alu_peak: GFLOP/s of FP64 fma, FP32 fma or packed FP32x2 fma on the current device."""
+    out = C.c_double(0.0)
+    s = lib().gpe_alu_peak(ALU_KINDS[kind], _stream_handle(stream), C.byref(out))
+    if s != GPE_OK:
+        raise GpeError(s, "gpe_alu_peak failed")
+    return out.value
 
 
 def solve_opts_default():

@@ -85,6 +85,38 @@ def harmonic_quartic(n, L, kappa, gammas=None):
     return harmonic(n, L, gammas) + 0.25 * kappa * r2 * r2
 
 
+def paper_harmonic(n, L, gammas=None):
+    """V_d^0 of eq. Lattice_Poten as printed for d = 2, 3: sum_nu gamma_nu nu^2
+    (gamma_nu = 1 by default).  With gamma = 1 this is r^2, twice the V = r^2/2
+    trap that Example eg:diff_initial_fix_grid states explicitly."""
+    m = mesh(n, L)
+    gammas = gammas or [1.0] * len(n)
+    return sum(g * xi * xi for g, xi in zip(gammas, m))
+
+
+def harmonic_plus_lattice(n, L, kappas, qs, gammas=None):
+    """eq. Lattice_Poten: V = V_d^0 + sum_nu kappa_nu sin^2(q_nu nu^2), the
+    argument nu^2 taken as printed (the 2D example of Section 6.2 uses
+    gamma = 1, kappa = 25, q = pi/2 on [-32, 32]^2)."""
+    m = mesh(n, L)
+    return paper_harmonic(n, L, gammas) + sum(k * np.sin(q * xi * xi) ** 2 for k, q, xi in zip(kappas, qs, m))
+
+
+def harmonic_plus_quartic(n, L, alpha, kappa, gammas=None, gamma_z=0.0):
+    """eq. Quart_Poten: V = (1 - alpha) V_2^0 + kappa (x^2 + y^2)^2 / 4, plus
+    gamma_z^2 z^2 in 3D, with V_2^0 = gamma_x x^2 + gamma_y y^2 as printed.
+    alpha > 1 makes the harmonic part repulsive (the double-well regime of
+    Section 6.2: alpha = 1.2, kappa = 0.3; 3D: alpha = 1.4, gamma_z = 3)."""
+    m = mesh(n, L)
+    g = gammas or [1.0, 1.0]
+    V = (1.0 - alpha) * (g[0] * m[0] ** 2 + g[1] * m[1] ** 2)
+    r2 = m[0] ** 2 + m[1] ** 2
+    V = V + 0.25 * kappa * r2 * r2
+    if len(n) == 3:
+        V = V + gamma_z ** 2 * m[2] ** 2
+    return V
+
+
 def smooth_bumps(n, L, seed, count=8):
     """Sum of `count` seeded Gaussian bumps scaled to max |S| = 1."""
     m = mesh(n, L)

@@ -2,8 +2,8 @@
 graph launch (gpe_batch_solve) against the same instances solved one at a
 time (gpe_pcg_solve, FP64 or mixed).
 
-    python -m paper_1611_02045_gb300.sweepbench --count 96 --steps 2
-    python -m paper_1611_02045_gb300.sweepbench --count 96 --single fp64
+    python sweepbench.py --count 96 --steps 2
+    python sweepbench.py --count 96 --single fp64
 
 Instances: inputs.sweep_instances (grids 128^2 / 256^2 / 512^2 on [-16,16]^2,
 omega ~ U[0, 0.95], eta in {100, 250, 500, 1000}, kappa in {0, 0.05}).

@@ -43,9 +43,9 @@ def test_ctypes_layout_matches_c(built_lib):
 #include "gpe.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(gpe_problem), offsetof(gpe_problem, eta), offsetof(gpe_problem, prec));
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(gpe_solve_opts), offsetof(gpe_solve_opts, switch_res), offsetof(gpe_solve_opts, use_graph),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gpe_solve_opts), offsetof(gpe_solve_opts, switch_res), offsetof(gpe_solve_opts, use_graph),
          offsetof(gpe_solve_opts, refine_restart), offsetof(gpe_solve_opts, precond), offsetof(gpe_solve_opts, beta_rule),
-         offsetof(gpe_solve_opts, line_search));
+         offsetof(gpe_solve_opts, line_search), offsetof(gpe_solve_opts, wait_polls));
   printf("%zu %zu %zu %zu %zu\n", sizeof(gpe_report), offsetof(gpe_report, res_l2), offsetof(gpe_report, log),
          offsetof(gpe_report, loop_kind), offsetof(gpe_report, iters_fp64));
   printf("%zu %zu %zu %zu\n", sizeof(gpe_tune_report), offsetof(gpe_tune_report, us_before),
@@ -63,7 +63,7 @@ int main(void) {
     want = [C.sizeof(G.gpe_problem), G.gpe_problem.eta.offset, G.gpe_problem.prec.offset,
             C.sizeof(G.gpe_solve_opts), G.gpe_solve_opts.switch_res.offset, G.gpe_solve_opts.use_graph.offset,
             G.gpe_solve_opts.refine_restart.offset, G.gpe_solve_opts.precond.offset, G.gpe_solve_opts.beta_rule.offset,
-            G.gpe_solve_opts.line_search.offset,
+            G.gpe_solve_opts.line_search.offset, G.gpe_solve_opts.wait_polls.offset,
             C.sizeof(G.gpe_report), G.gpe_report.res_l2.offset, G.gpe_report.log.offset,
             G.gpe_report.loop_kind.offset, G.gpe_report.iters_fp64.offset,
             C.sizeof(G.gpe_tune_report), G.gpe_tune_report.us_before.offset, G.gpe_tune_report.E.offset,
@@ -76,6 +76,7 @@ def test_solve_opts_defaults(built_lib):
     assert o.tol_res_inf == 1e-8 and o.max_iter == 20000 and o.theta_default == 0.1
     assert o.max_backtracks == 30 and o.cg == 1 and o.use_graph == 3 and o.refine_restart == 1
     assert o.precond == G.GPE_PRECOND_C and o.beta_rule == G.GPE_BETA_PR and o.line_search == G.GPE_LINE_MODEL
+    assert o.wait_polls == 0
     assert G.lib().gpe_solve_opts_default(None) == G.GPE_ERR_ARG
 
 

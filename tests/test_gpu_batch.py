@@ -79,7 +79,7 @@ def test_batch_reproduces_single_instance_solves(G):
         po = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
         ph = ph1.astype(np.complex128)
         lam = O.chemical_potential(po, ph)
-        assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+        assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8
         assert abs(O.energy(po, ph) - rb["E"]) <= 1e-12 * abs(rb["E"])
 
 
@@ -92,7 +92,7 @@ def test_stalled_refinement_is_completed_in_fp64(G):
     assert rep["status"] == G.GPE_OK and rep["iters_fp64"] > 0, rep
     po = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
     lam = O.chemical_potential(po, ph)
-    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8
 
 
 def test_batch_with_3d_instances(G):

@@ -90,6 +90,6 @@ def test_multigrid_solve_reaches_a_verified_ground_state(G):
     po = O.Problem(w["n"], w["L"], w["eta"], w["omega"], w["V"])
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
-    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8
     assert abs(O.energy(po, ph) - reps[-1]["E"]) <= 1e-12 * abs(reps[-1]["E"])
     assert abs(O.norm(po, ph) - 1.0) < 1e-12

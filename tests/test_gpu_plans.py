@@ -152,7 +152,7 @@ def test_autotuned_mixed_solve(G, name):
     assert rep["status"] == G.GPE_OK and rep["res_inf"] < 1e-8
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
-    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8
     assert abs(O.energy(po, ph) - rep["E"]) <= 1e-12 * abs(rep["E"])
     if name == "c64_2d":
         _, orep = O.pcg_solve(po, w["phi0"], O.SolveOptions())

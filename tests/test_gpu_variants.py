@@ -92,7 +92,7 @@ def test_mixed_cluster_solve_with_variants(G, precond):
     assert abs(rep["E"] - orep["E"]) <= 1e-7 * abs(orep["E"])
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
-    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8
 
 
 def test_bad_variant_options_are_rejected(G):
@@ -171,4 +171,4 @@ def test_thomas_fermi_state_matches_oracle(G, case):
     assert rep["status"] == G.GPE_OK, rep
     ph = host(phi)
     lam = O.chemical_potential(po, ph)
-    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1.05e-8
+    assert np.max(np.abs(O.apply_H(po, ph, ph) - lam * ph)) < 1e-8

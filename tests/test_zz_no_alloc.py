@@ -81,3 +81,20 @@ def test_noalloc_rejects_grids_beyond_its_scratch(G):
     p.n[0] = 12
     s, msg = noalloc(G, p, x, x, x, x)
     assert s == G.GPE_ERR_ARG and msg
+
+
+def test_noalloc_rejects_grids_beyond_its_block_limit_before_any_work(G):
+    """512 x 8 x 512 complex64 fits the 16 MiB field (2^21 points) but its y
+    pass needs 16384 thread blocks, more than the 8192 the scratch partials
+    hold: rejected up front, out left as it was."""
+    n, L = (512, 8, 512), (8.0, 8.0, 8.0)
+    p = problem(G, n, L, 1.0, 0.0, 1)
+    N = 512 * 8 * 512
+    V = torch.zeros(N, dtype=torch.float32, device="cuda")
+    x = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    out = torch.full((N,), 7.0 + 3.0j, dtype=torch.complex64, device="cuda")
+    s, msg = noalloc(G, p, V, x, x, out)
+    assert s == G.GPE_ERR_UNSUPPORTED, msg
+    assert "thread blocks" in msg
+    torch.cuda.synchronize()
+    assert bool(torch.all(out == (7.0 + 3.0j)))
