@@ -407,6 +407,40 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     del hphi, hout
 
+    # ---------------- arithmetic-pipe rates and the FP64 roof ----------------
+    # FP64 mode is bound by the FP64 pipe, not by HBM: H phi in FP64 on a 256^3 complex128
+    # field (268 MB in, 268 MB out), flops by the nominal 5 M log2 M model per line transform
+    # (3 axes x forward + inverse) plus 20 flops per point for the multipliers and the real-space
+    # term, against the measured FP64 fma rate.
+    alu = {k: gpe.alu_peak(k) for k in ("fp64_fma", "fp32_fma", "fp32x2_fma")}
+    fp64_roof = None
+    if rank == 0:
+        n3, L3 = (256, 256, 256), (8.0, 8.0, 8.0)
+        N3 = int(np.prod(n3))
+        with gpe.Context(n3, L3, 5000.0, 0.8, I.harmonic(n3, L3, [1.0, 1.0, 2.0]), prec=gpe.GPE_FP64) as c3:
+            g3 = torch.Generator(device=dev).manual_seed(3)
+            x3 = torch.randn(N3, dtype=torch.complex128, device=dev, generator=g3)
+            y3 = torch.empty_like(x3)
+            for _ in range(2):
+                c3.apply_H(x3, x3, y3)
+            t3 = []
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                c3.apply_H(x3, x3, y3)
+                b.record(stream)
+                b.synchronize()
+                t3.append(a.elapsed_time(b))
+            del x3, y3
+        ms3 = statistics.median(t3)
+        flops3 = (3 * 2 * 5 * 8 + 20) * N3
+        ach = flops3 / (ms3 * 1e-3) / 1e9
+        fp64_roof = {"kernel": "gpe_apply_H, GPE_FP64, 256^3 complex128 (x, y, z pass kernels)", "bound": "fp64_alu",
+                     "achieved": ach, "peak": alu["fp64_fma"], "unit": "GFLOP/s", "frac": ach / alu["fp64_fma"],
+                     "ms_per_call": ms3, "hbm_gbs_algorithmic": 40.0 * N3 / (ms3 * 1e-3) / 1e9,
+                     "flop_model": "5 M log2 M per line transform x 6 transforms + 20 per point",
+                     "peak_source": "gpe_alu_peak(fp64 fma), measured in this run"}
+
     # ---------------- secondary: the 128^3 workload ----------------
     secondary = None
     if not args.no_secondary:
@@ -437,8 +471,9 @@ def main():
     # graph launch; no data-path collective, the reports are combined on the host.
     batch = None
     if not args.no_batch:
+        from paper_1611_02045_gb300.replicas import instance_share, sum_over_ranks
         insts_all = I.sweep_instances(96)
-        mine = [i for i in range(len(insts_all)) if i % world == rank]
+        mine = instance_share(len(insts_all), rank, world)
         insts = [insts_all[i] for i in mine]
         arrays = [I.sweep_arrays(x) for x in insts]
         specs = [dict(n=x["n"], L=x["L"], eta=x["eta"], omega=x["omega"], V=V, prec=gpe.GPE_MIXED)
@@ -482,10 +517,7 @@ def main():
                     fp64_ok += r1["status"] == gpe.GPE_OK
             fp64_ms = max_over_ranks(fp64_ms, dev)
             counts.append(fp64_ok)
-        if world > 1:
-            t = torch.tensor(counts, dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t)
-            counts = [int(v) for v in t.tolist()]
+        counts = [int(v) for v in sum_over_ranks(counts, dev)]
         batch = {"workload": "sweep96_2d (32 each of 128^2, 256^2, 512^2 on [-16,16]^2; omega U[0,0.95], "
                              "eta {100,250,500,1000}, kappa {0,0.05})",
                  "value": 96 * 1000.0 / bms, "unit": UNIT, "ms_per_step": bms,
@@ -650,6 +682,8 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "accuracy": accuracy,
+            "alu_peaks_gflops": alu,
+            "fp64_roofline": fp64_roof,
             "cpu_baseline": cpu,
             "secondary": secondary,
             "batch": batch,
