@@ -32,9 +32,15 @@ phi already in device memory.  Alongside it the line reports:
 """
 from __future__ import annotations
 
+import os
+
+# The CPU oracle legs count host threads exactly: numpy's BLAS runs one thread per
+# process (set before numpy loads; spawned oracle processes inherit it).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
