@@ -182,11 +182,33 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // of M/32 CTAs, one 512-thread CTA per SM at M = 256 with E = 16).
 template <typename T, int RR> struct StreamMinBlocks { static constexpr int value = RR == 16 ? ClusterMinBlocks<T>::value : 1; };
 
+// Exchange layout of the x part: row l, position p at l * XLS + p + XP * (p / 16).
+// At M = 256 with E = 16 the pad is 2 per 16 (16-byte aligned runs of 16 for
+// the vector stores of dft256x16), else 1 per 16.  (Column transforms kept
+// inside one warp -- two columns per warp, padded row buffers -- were measured
+// 2x slower: their cluster gathers and output stores touch 16 rows per warp
+// instruction instead of two contiguous 128-byte segments.)
+template <int M, int EV> struct StreamX {
+  static constexpr bool fast = (M == 256 && EV == 16);
+  static constexpr int XP = fast ? 2 : 1;
+  static constexpr int XLS = M + XP * (M / 16);
+  static constexpr int RS = M;
+};
+template <typename T, int M, int EV, int RR> struct StreamSmem {
+  using C = cplx<T>;
+  static constexpr size_t rows = (size_t)2 * RR * StreamX<M, EV>::RS * sizeof(C);
+  static constexpr size_t xs = (size_t)RR * StreamX<M, EV>::XLS * sizeof(C);  // >= M * RR (y part)
+  static constexpr size_t tws = StreamX<M, EV>::fast ? (size_t)16 * kTw256Stride * sizeof(float4) : 0;
+  static constexpr size_t bytes = rows + xs + tws;
+};
+
 template <typename T, int M, int EV, int RR>
 __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
     cluster_apply_H_stream(ClusterHArgs a) {
   using C = cplx<T>;
-  constexpr int E = EV, Tl = M / EV, R = RR, LS = M + M / 16;
+  constexpr int E = EV, Tl = M / EV, R = RR;
+  constexpr bool FAST = StreamX<M, EV>::fast;
+  constexpr int XP = StreamX<M, EV>::XP, XLS = StreamX<M, EV>::XLS, RS = StreamX<M, EV>::RS;
   constexpr int NT = Tl * R;  // threads per CTA
   static_assert(Tl <= 32 && (32 % Tl) == 0, "a row's threads lie inside one warp");
   cg::cluster_group cl = cg::this_cluster();
@@ -194,8 +216,9 @@ __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
   const int csize = (int)cl.num_blocks();
   const long long cid = blockIdx.x / csize, ncl = gridDim.x / csize;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* rows = reinterpret_cast<C*>(smraw);  // [2][R][M] row buffers
-  C* xs = rows + 2 * R * M;                // [R][LS] (x) or [M][R] (y) exchange
+  C* rows = reinterpret_cast<C*>(smraw);  // [2][R][RS] row buffers
+  C* xs = rows + 2 * R * RS;               // [R][XLS] (x), [M][R] or [R][XLS] (y) exchange
+  float4* tws = reinterpret_cast<float4*>(smraw + StreamSmem<T, M, EV, RR>::rows + StreamSmem<T, M, EV, RR>::xs);
   const C* __restrict__ f = static_cast<const C*>(a.f);
   const C* __restrict__ phi = static_cast<const C*>(a.phi);
   const T* __restrict__ V = static_cast<const T*>(a.V);
@@ -206,20 +229,24 @@ __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
   const T invM = T(1) / T(M);
   const T om = T(a.omega), eta = T(a.eta);
   const bool same = (a.f == a.phi);
+  if constexpr (FAST) dft256_twiddles(tws, reinterpret_cast<const float2*>(tw));  // read after the first barrier
 
-  // rows 16 rank .. 16 rank + 15 of field fld: R M contiguous elements
+  // rows R rank .. R rank + R - 1 of field fld (R M contiguous elements) into rows of stride RS
   auto fetch = [&](long long fld, C* dst) {
     const char* src = reinterpret_cast<const char*>(f + fld * a.stride + (long long)rank * R * M);
     char* d = reinterpret_cast<char*>(dst);
-    constexpr int chunks = R * M * (int)sizeof(C) / 16;
-    for (int i = threadIdx.x; i < chunks; i += NT) cp_async16(d + 16 * i, src + 16 * (long long)i);
+    constexpr int per_row = M * (int)sizeof(C) / 16, chunks = R * per_row;
+    for (int i = threadIdx.x; i < chunks; i += NT) {
+      const int r = i / per_row, j = i - r * per_row;
+      cp_async16(d + (size_t)r * RS * sizeof(C) + 16 * j, src + 16 * (long long)i);
+    }
     cp_async_commit();
   };
   if (cid < a.nbatch) fetch(cid, rows);
   int k = 0;
   for (long long fld = cid; fld < a.nbatch; fld += ncl, ++k) {
-    C* fs = rows + (k & 1) * R * M;
-    C* fn = rows + ((k & 1) ^ 1) * R * M;
+    C* fs = rows + (k & 1) * R * RS;
+    C* fn = rows + ((k & 1) ^ 1) * R * RS;
     cp_async_wait_all();
     __syncthreads();  // rows(k) complete in fs; every warp is done with xs (y part of k - 1)
     const long long fb = fld * a.stride;
@@ -229,7 +256,7 @@ __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
       const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
       const int y = rank * R + l;
       // row bases once: the per-q offsets q Tl below are compile-time constants
-      const C* frow = fs + l * M + t;
+      const C* frow = fs + l * RS + t;
       const T* Vrow = V + y * M + t;
       C* orow = out + fb + (long long)y * M + t;
       C w[E];
@@ -240,15 +267,17 @@ __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
         const C ph = same ? w[q] : phi[fb + (long long)y * M + t + q * Tl];
         m[q] = Vrow[q * Tl] + eta * (ph.x * ph.x + ph.y * ph.y);
       }
-      auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
-      line_dft<M, E, -1, true>(w, xs, si, t, tw);
+      auto si = [l](int pos) { return l * XLS + pos + XP * (pos >> 4); };
+      if constexpr (FAST) dft256x16<-1, true, true>(w, xs, si, t, tws);
+      else line_dft<M, E, -1, true>(w, xs, si, t, tw);
       const T yy = static_cast<const T*>(a.yc)[y];
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const T kx = xi[t + q * Tl];
         w[q] = cscale(w[q], (T(0.5) * kx * kx + om * yy * kx) * invM);
       }
-      line_dft<M, E, +1, true>(w, xs, si, t, tw);
+      if constexpr (FAST) dft256x16<+1, true, true>(w, xs, si, t, tws);
+      else line_dft<M, E, +1, true>(w, xs, si, t, tw);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const C v = frow[q * Tl];
@@ -258,33 +287,37 @@ __global__ void __launch_bounds__((M / EV) * RR, StreamMinBlocks<T, RR>::value)
     cl.sync();  // rows(k) of every CTA visible; t rows stored; y parts of k - 1 finished
     if (fld + ncl < a.nbatch) fetch(fld + ncl, fn);
 
-    // ---- y part: columns 16 rank .. 16 rank + 15, rows gathered from the cluster ----
+    // ---- y part: columns R rank .. R rank + R - 1, rows gathered from the cluster ----
     {
       const int c = threadIdx.x % R, t = threadIdx.x / R;
       const int x = rank * R + c;
+      C* ocol = out + fb + (long long)t * M + x;
       // row y = t + q Tl lives in CTA y / R at local row y % R
-      C w[E];
+      C w[E], tv[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int y = t + q * Tl;
         const C* src = cl.map_shared_rank(fs, (unsigned)(y / R));
-        w[q] = src[(y % R) * M + x];
+        w[q] = src[(y % R) * RS + x];
       }
+      // t = A_x f + (V + eta|phi|^2) f of these columns, stored by the rows' owners before
+      // the barrier: loaded now so that the loads overlap the transforms
+#pragma unroll
+      for (int q = 0; q < E; ++q) tv[q] = __ldcg(ocol + q * Tl * M);
       auto si = [c](int pos) { return pos * R + c; };
-      line_dft<M, E, -1>(w, xs, si, t, tw);  // its first barrier retires the x part's use of xs
+      // the first barrier of the transform retires the x part's use of xs
+      if constexpr (FAST) dft256x16<-1, false, false>(w, xs, si, t, tws);
+      else line_dft<M, E, -1>(w, xs, si, t, tw);
       const T xx = static_cast<const T*>(a.xc)[x];
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const T ky = xiy[t + q * Tl];
         w[q] = cscale(w[q], (T(0.5) * ky * ky - om * xx * ky) * invM);
       }
-      line_dft<M, E, +1>(w, xs, si, t, tw);
-      C* ocol = out + fb + (long long)t * M + x;
+      if constexpr (FAST) dft256x16<+1, false, false>(w, xs, si, t, tws);
+      else line_dft<M, E, +1>(w, xs, si, t, tw);
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const C o = __ldcg(ocol + q * Tl * M);  // t, stored by the row's owner before the barrier
-        ocol[q * Tl * M] = cadd(o, w[q]);
-      }
+      for (int q = 0; q < E; ++q) ocol[q * Tl * M] = cadd(tv[q], w[q]);
     }
   }
   cl.sync();  // no CTA leaves while others may still gather from its rows
@@ -333,7 +366,7 @@ cudaError_t launch_cluster_apply_H_stream(const ClusterHArgs& a, cudaStream_t st
   constexpr int R = RR;
   const int csize = M / R;
   const int threads = (M / EV) * R;
-  const size_t smem = (size_t)(2 * R * M + R * (M + M / 16)) * sizeof(cplx<T>);
+  const size_t smem = StreamSmem<T, M, EV, RR>::bytes;
   auto kern = cluster_apply_H_stream<T, M, EV, RR>;
   static std::atomic<int> max_clusters_dev[64];  // per device; 0 = not yet queried
   const int dev = DeviceOnce::device();

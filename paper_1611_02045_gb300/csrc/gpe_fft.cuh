@@ -200,6 +200,53 @@ __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t
   }
 }
 
+// ---------------------------------------------------------------------------
+// 256-point complex64 line by 16 threads of 16 values: the same radix-16 x 16
+// Stockham transform as line_dft<256, 16>, with
+//  * the 15 stage-2 twiddles e^{-2 pi i t r/256} (r = 1..15) of thread t read
+//    from a shared table tws (dft256_twiddles), two per 16-byte load;
+//  * with VEC, the stage-1 results (positions 16t .. 16t+15, contiguous and
+//    16-byte aligned in the exchange layout si) stored as 16-byte pairs.
+// v[q] = f[t + 16 q] on entry, F[f][t + 16 q] on return (DIR = -1 forward,
+// +1 inverse unnormalised).  Every thread of the line group must call it.
+// ---------------------------------------------------------------------------
+constexpr int kTw256Stride = 9;  // float4 per thread row of the table (8 used + 1 pad: no bank conflicts)
+
+// Fill tws[t * 9 + i] = {w(t, 2i), w(t, 2i + 1)} with w(t, r) = tw[(t r) mod 256]
+// (tw: the e^{-2 pi i m / 256} table); caller synchronises before use.
+__device__ __forceinline__ void dft256_twiddles(float4* tws, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < 16 * 8; i += blockDim.x) {
+    const int t = i >> 3, r = 2 * (i & 7);
+    const float2 a = tw[(t * r) & 255], b = tw[(t * (r + 1)) & 255];
+    tws[t * kTw256Stride + (i & 7)] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+template <int DIR, bool WARP, bool VEC, typename SI>
+__device__ __forceinline__ void dft256x16(float2 (&v)[16], float2* sm, const SI& si, int t, const float4* tws) {
+  dft16<DIR>(v);
+  line_sync<WARP>();  // previous readers of sm are done
+  if constexpr (VEC) {
+    float4* d = reinterpret_cast<float4*>(sm + si(16 * t));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[si(16 * t + r)] = v[r];
+  }
+  line_sync<WARP>();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[si(t + 16 * q)];
+  const float4* w = tws + t * kTw256Stride;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 p = w[i];
+    if (i > 0) v[2 * i] = ctw<DIR>(v[2 * i], make_float2(p.x, p.y));
+    v[2 * i + 1] = ctw<DIR>(v[2 * i + 1], make_float2(p.z, p.w));
+  }
+  dft16<DIR>(v);
+}
+
 // Forward (DIR = -1) or inverse-unnormalised (DIR = +1) DFT of one line held
 // as v[q] = f[t + q*Tl]; on return v[q] = F[f][t + q*Tl].  Every thread of the
 // block (WARP: of the warp) must call it: it contains the stage barriers.
