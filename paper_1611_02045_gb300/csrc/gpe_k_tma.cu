@@ -1,0 +1,462 @@
+// gpe_k_tma.cu -- the passes of H_phi f (Section 2 operator, eq. FFTdiscret of
+// Section 3) in complex64 fed by the Tensor Memory Accelerator:
+//  * y / z (role P_HMID): t += IFFT_axis[ (1/2 k^2 - omega x k) FFT_axis f ],
+//    the arithmetic of pass_s<float, M, P_HMID>, column tiles through 3D
+//    tensor-map boxes;
+//  * x (role P_HX): t = IFFT_x[ (1/2 xi^2 + omega y xi) FFT_x f ] + (V + eta|phi|^2) f
+//    with the solver's retraction folded in, the arithmetic of
+//    pass_x<float, float, float, M, P_HX>, rows through 1D bulk copies.
+//
+// A strided pass touches a tile of tx adjacent x-columns along the whole
+// transformed axis (rows of tx * 8 bytes, a field row apart).  Here each block
+// is persistent: it walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...,
+// and while it transforms one tile, the TMA unit copies the next tile's f and
+// t columns (3D tensor-map boxes, at most 256 rows per box) into the other of
+// two shared-memory stages, completing on that stage's mbarrier.  The loads
+// therefore overlap the transforms, which the one-tile-per-block kernel
+// cannot do.  Every mbarrier wait is bounded: a wait that gives up marks the
+// solve (or API call) GPE_ERR_TIMEOUT in the control block, waits (bounded)
+// for the block's copy still in flight, and the block joins the reduction
+// with what it has, so that no kernel hangs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "gpe_passes.cuh"
+
+namespace gpe {
+
+namespace {
+
+constexpr long long kTmaWaitLimit = 1ll << 24;  // try_wait polls (each may suspend briefly): seconds
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// true when the phase with the given parity has completed; false after the bound.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (long long n = 0; n < kTmaWaitLimit; ++n) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 3D tile load global -> shared through the tensor map, completing on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Contiguous global -> shared bulk copy (16-byte aligned, size a multiple of 16),
+// completing on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <int M, int EV>
+__global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_constant__ CUtensorMap tmf,
+                                                      const __grid_constant__ CUtensorMap tmt) {
+  using T = float;
+  using C = float2;
+  constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
+  constexpr int BOX = M < 256 ? M : 256;  // rows per tensor-map box
+  constexpr int NBOX = M / BOX;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  if (a.solver && a.ctl->done) return;
+  const int tx = a.tx;
+  const int tile = M * tx;  // elements of one column tile
+  C* stage = reinterpret_cast<C*>(smraw);  // [2 stages][f tile, t tile]
+  C* ex = stage + 4 * tile;                // transform exchange [M][tx]
+  const int c = threadIdx.x % tx, t = threadIdx.x / tx;
+  const long long units = a.nblocks;
+  const unsigned bytes = 2u * (unsigned)tile * (unsigned)sizeof(C);
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // f and t columns of tile u into stage s (one thread)
+  auto issue = [&](long long u, int s) {
+    const int xt = (int)(u % a.ntx);
+    const int outer = (int)(u / a.ntx);
+    C* fdst = stage + (2 * s) * tile;
+    C* tdst = fdst + tile;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stage's earlier generic reads
+    mbar_expect_tx(&bar[s], bytes);
+#pragma unroll
+    for (int b = 0; b < NBOX; ++b) {
+      const int x0 = xt * tx;
+      const int y0 = a.axis == 1 ? b * BOX : outer;
+      const int z0 = a.axis == 1 ? outer : b * BOX;
+      tma_load_3d(fdst + b * BOX * tx, &tmf, x0, y0, z0, &bar[s]);
+      tma_load_3d(tdst + b * BOX * tx, &tmt, x0, y0, z0, &bar[s]);
+    }
+  };
+
+  Acc acc[kMaxMoments];
+#pragma unroll
+  for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const T* __restrict__ xia = tab<T>(a.xi[a.axis]);
+  const T invM = T(1) / T(M);
+  const T om = T(a.omega);
+  auto si = [tx, c](int pos) { return pos * tx + c; };
+  C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: the final pass writes the caller's buffer
+
+  if (threadIdx.x == 0 && (long long)blockIdx.x < units) issue(blockIdx.x, 0);
+  int i = 0;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool next = u + gridDim.x < units;
+    if (threadIdx.x == 0 && next) issue(u + gridDim.x, s ^ 1);
+    const bool ok = mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      // give up: report, wait (bounded) for this block's copies still in flight, and
+      // join the reduction with what the block has
+      if (threadIdx.x == 0) {
+        atomicExch(&a.ctl->status, 6);  // GPE_ERR_TIMEOUT
+        atomicExch(&a.ctl->done, 1);
+        mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+        if (next) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      break;
+    }
+    const C* fs = stage + (2 * s) * tile;
+    const C* ts = fs + tile;
+    const int xt = (int)(u % a.ntx);
+    const int ix = xt * tx + c;
+    const long long base = (u / a.ntx) * a.outer_stride + ix;
+    C v[E], tv[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      v[q] = fs[(t + q * Tl) * tx + c];
+      tv[q] = ts[(t + q * Tl) * tx + c];
+    }
+    line_dft<M, E, -1>(v, ex, si, t, tw);
+    const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
+    const T rx = (a.axis == 1) ? -x : T(0);  // rotation symbol -omega x mu (y); none for z
+    T akin = 0, arot = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xia[t + q * Tl];
+      const T mk = T(0.5) * k * k, kr = rx * k;
+      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+      akin += mk * a2;
+      arot += kr * a2;
+      v[q] = cscale(v[q], (mk + om * kr) * invM);
+    }
+    line_dft<M, E, +1>(v, ex, si, t, tw);
+#pragma unroll
+    for (int q = 0; q < E; ++q) dst[base + (t + q * Tl) * a.stride] = cadd(tv[q], v[q]);
+    acc[0] = acc_add(acc[0], acc_from(akin * invM));
+    acc[1] = acc_add(acc[1], acc_from(arot * invM));
+    __syncthreads();  // stage s is read by every thread before it is refilled
+  }
+  reduce_and_finish<P_HMID>(a, acc);
+}
+
+// x pass of H phi: blocks of lpb whole lines (rows), persistent over the units
+// blockIdx.x, blockIdx.x + gridDim.x, ...; stage s holds the unit's phi rows,
+// its second operand (f in an API call with f != phi, p in a solve with the
+// retraction) and its V rows, copied in by one thread while the previous unit
+// is transformed.
+template <int M, int EV>
+__global__ void __launch_bounds__(512) pass_hx_bulk(PassArgs a, int second) {
+  using T = float;
+  using C = float2;
+  constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
+  constexpr int LS = M + M / 16;
+  constexpr bool W = Tl <= 32;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  if (a.solver && a.ctl->done) return;
+  const Scal S = scal_of(a.ctl, a);
+  const int lpb = a.lpb;
+  const int rows = lpb * M;  // elements of one unit
+  const size_t cbytes = (size_t)rows * sizeof(C), vbytes = (size_t)rows * sizeof(T);
+  const size_t sbytes = 2 * cbytes + vbytes;  // one stage
+  unsigned char* stage0 = smraw;
+  C* sm = reinterpret_cast<C*>(smraw + 2 * sbytes);  // transform exchange [lpb][LS]
+  const int t = threadIdx.x % Tl, l = threadIdx.x / Tl;
+  const long long units = a.nblocks;
+  const C* __restrict__ phi = static_cast<const C*>(a.phi);
+  const C* __restrict__ sec = static_cast<const C*>(second == 1 ? a.f : a.p);  // 0: no second operand
+  const T* __restrict__ V = tab<T>(a.V);
+  const unsigned bytes = (unsigned)((second ? 2 : 1) * cbytes + vbytes);
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](long long u, int s) {
+    unsigned char* d = stage0 + s * sbytes;
+    const long long e0 = u * rows;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[s], bytes);
+    bulk_load(d, phi + e0, (unsigned)cbytes, &bar[s]);
+    if (second) bulk_load(d + cbytes, sec + e0, (unsigned)cbytes, &bar[s]);
+    bulk_load(d + 2 * cbytes, V + e0, (unsigned)vbytes, &bar[s]);
+  };
+
+  Acc acc[kMaxMoments];
+#pragma unroll
+  for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const T* __restrict__ xi = tab<T>(a.xi[0]);
+  const T invM = T(1) / T(M);
+  const T om = T(a.omega), eta = T(a.eta);
+  auto si = [l](int pos) { return l * LS + pos + (pos >> 4); };
+  const bool retract = a.solver && S.retract;
+  const T cc = T(retract ? S.c * S.inv_nrm : 1.0);
+  const T ss = T(retract ? S.s * S.inv_np * S.inv_nrm : 0.0);
+  C* __restrict__ phi_out = static_cast<C*>(a.phi_out);
+  C* __restrict__ tout = static_cast<C*>(a.t);
+
+  if (threadIdx.x == 0 && (long long)blockIdx.x < units) issue(blockIdx.x, 0);
+  int i = 0;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool next = u + gridDim.x < units;
+    if (threadIdx.x == 0 && next) issue(u + gridDim.x, s ^ 1);
+    const bool ok = mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(&a.ctl->status, 6);  // GPE_ERR_TIMEOUT
+        atomicExch(&a.ctl->done, 1);
+        mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+        if (next) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      break;
+    }
+    const unsigned char* d = stage0 + s * sbytes;
+    const C* phs = reinterpret_cast<const C*>(d) + l * M + t;
+    const C* secs = reinterpret_cast<const C*>(d + cbytes) + l * M + t;
+    const T* vs = reinterpret_cast<const T*>(d + 2 * cbytes) + l * M + t;
+    const long long line = u * lpb + l;
+    const long long base = line * M + t;
+    const int iy = (int)((a.row0 + line) % a.ny);
+    C ph[E], v[E];
+    T vv[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      C x = phs[q * Tl];
+      if (retract) {
+        const C pq = secs[q * Tl];
+        x = make_float2(cc * x.x + ss * pq.x, cc * x.y + ss * pq.y);
+        phi_out[base + q * Tl] = x;
+      }
+      ph[q] = x;
+      vv[q] = vs[q * Tl];
+      v[q] = (second == 1) ? secs[q * Tl] : x;
+    }
+    line_dft<M, E, -1, W>(v, sm, si, t, tw);
+    const T y = tab<T>(a.xc[1])[iy];
+    T akin = 0, arot = 0;  // arot: the rotation symbol without omega (omega is applied in finalize_H)
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T k = xi[t + q * Tl];
+      const T mk = T(0.5) * k * k, kr = y * k;
+      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+      akin += mk * a2;
+      arot += kr * a2;
+      v[q] = cscale(v[q], (mk + om * kr) * invM);
+    }
+    line_dft<M, E, +1, W>(v, sm, si, t, tw);
+    T apot = 0, au2 = 0, an2 = 0, umax = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T uu = ph[q].x * ph[q].x + ph[q].y * ph[q].y;
+      const T m = vv[q] + eta * uu;
+      const C fq = (second == 1) ? secs[q * Tl] : ph[q];  // the operand f (API call with f != phi)
+      tout[base + q * Tl] = make_float2(v[q].x + m * fq.x, v[q].y + m * fq.y);
+      apot += vv[q] * uu;
+      au2 += uu * uu;
+      an2 += uu;
+      umax = fmaxf(umax, uu);
+    }
+    acc[0] = acc_add(acc[0], acc_from(akin * invM));
+    acc[1] = acc_add(acc[1], acc_from(arot * invM));
+    acc[2] = acc_add(acc[2], acc_from(apot));
+    acc[3] = acc_add(acc[3], acc_from(au2));
+    acc[4] = acc_add(acc[4], acc_from(an2));
+    acc[5] = acc_max(acc[5], acc_from(umax));
+    __syncthreads();  // stage s is read by every thread before it is refilled
+  }
+  reduce_and_finish<P_HX>(a, acc);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map over a complex64 field [nz][ny][nx] (8-byte elements), boxes of
+// tx x-columns along the pass axis (BOX rows).
+bool encode_field(CUtensorMap* m, const void* base, const PassArgs& a, int box) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 8, (cuuint64_t)a.nx * a.ny * 8};
+  const cuuint32_t boxd[3] = {(cuuint32_t)a.tx, (cuuint32_t)(a.axis == 1 ? box : 1), (cuuint32_t)(a.axis == 1 ? 1 : box)};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, boxd, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int M, int EV>
+cudaError_t launch_tma_one(const PassArgs& a, cudaStream_t st, bool* used) {
+  constexpr int Tl = LineCfg<M, EV>::Tl;
+  const int threads = Tl * a.tx;
+  if (threads > 512 || a.tx < 2 || (a.tx & 1)) return cudaSuccess;  // 16-byte rows: tx even
+  const size_t smem = (size_t)5 * M * a.tx * sizeof(float2);
+  if (smem > 200 * 1024) return cudaSuccess;
+  const void* fsrc = (a.f && !a.solver) ? a.f : a.phi;
+  if ((reinterpret_cast<uintptr_t>(fsrc) & 15u) || (reinterpret_cast<uintptr_t>(a.t) & 15u)) return cudaSuccess;
+  CUtensorMap tmf, tmt;
+  constexpr int BOX = M < 256 ? M : 256;
+  if (!encode_field(&tmf, fsrc, a, BOX) || !encode_field(&tmt, a.t, a, BOX)) return cudaSuccess;
+  auto kern = pass_hmid_tma<M, EV>;
+  static DeviceOnce attr;
+  static std::atomic<int> occ_dev[64][2];  // blocks per SM, per device and tx class (0 = unknown)
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr.set(dev);
+  }
+  const int cls = a.tx >= 8 ? 1 : 0;
+  int occ = (dev >= 0 && dev < 64) ? occ_dev[dev][cls].load() : 0;
+  if (occ <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess || occ < 1) { cudaGetLastError(); return cudaSuccess; }
+    if (dev >= 0 && dev < 64) occ_dev[dev][cls].store(occ);
+  }
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaGetLastError();
+  long long grid = (long long)occ * nsm;
+  if (grid > a.nblocks) grid = a.nblocks;
+  *used = true;
+  kern<<<(unsigned)grid, threads, smem, st>>>(a, tmf, tmt);
+  return cudaGetLastError();
+}
+
+template <int M, int EV>
+cudaError_t launch_hx_one(const PassArgs& a0, cudaStream_t st, bool* used) {
+  constexpr int Tl = LineCfg<M, EV>::Tl;
+  PassArgs a = a0;
+  // 256 threads per block: lpb = 256 / Tl whole lines per unit
+  const long long nlines = (long long)a.ny * a.nz;
+  int lpb = 256 / Tl;
+  while (lpb > 1 && nlines % lpb) lpb >>= 1;
+  if (lpb < 1 || nlines / lpb < 1) return cudaSuccess;
+  a.lpb = lpb;
+  a.nblocks = (int)(nlines / lpb);
+  const int threads = Tl * lpb;
+  // second operand: f (API call with f != phi: 1) or p (solve with the retraction: 2)
+  const int second = (!a.solver && a.f && a.f != a.phi) ? 1 : (a.solver ? 2 : 0);
+  const size_t cb = (size_t)lpb * M * sizeof(float2), vb = (size_t)lpb * M * sizeof(float);
+  const size_t smem = 2 * (2 * cb + vb) + (size_t)lpb * (M + M / 16) * sizeof(float2);
+  if (smem > 200 * 1024 || (cb & 15) || (vb & 15)) return cudaSuccess;
+  const void* ptrs[3] = {a.phi, second == 1 ? a.f : (second == 2 ? a.p : a.phi), a.V};
+  for (const void* q : ptrs)
+    if (reinterpret_cast<uintptr_t>(q) & 15u) return cudaSuccess;
+  auto kern = pass_hx_bulk<M, EV>;
+  static DeviceOnce attr;
+  static std::atomic<int> occ_dev[64];
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr.set(dev);
+  }
+  int occ = (dev >= 0 && dev < 64) ? occ_dev[dev].load() : 0;
+  if (occ <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess || occ < 1) { cudaGetLastError(); return cudaSuccess; }
+    if (dev >= 0 && dev < 64) occ_dev[dev].store(occ);
+  }
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaGetLastError();
+  long long grid = (long long)occ * nsm;
+  if (grid > a.nblocks) grid = a.nblocks;
+  *used = true;
+  kern<<<(unsigned)grid, threads, smem, st>>>(a, second);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// x pass of H phi in complex64 through the bulk-copy pipeline (M in 64 .. 512,
+// 16-byte aligned phi, f or p and V, E = 8); *used = false otherwise.
+cudaError_t launch_hx_bulk(const PassArgs& a, cudaStream_t st, bool* used) {
+  *used = false;
+  if (a.E != 0 && a.E != 8) return cudaSuccess;
+  if (a.row0 != 0) return cudaSuccess;
+  switch (a.M) {
+    case 64: return launch_hx_one<64, 8>(a, st, used);
+    case 128: return launch_hx_one<128, 8>(a, st, used);
+    case 256: return launch_hx_one<256, 8>(a, st, used);
+    case 512: return launch_hx_one<512, 8>(a, st, used);
+    default: return cudaSuccess;
+  }
+}
+
+// y / z pass of H phi in complex64 through the TMA pipeline when the plan and
+// the fields allow it (E = 8, even tile width, 16-byte aligned f and t,
+// M in {64, 128, 256, 512}); *used = false otherwise (the caller launches
+// pass_s).
+cudaError_t launch_hmid_tma(const PassArgs& a, cudaStream_t st, bool* used) {
+  *used = false;
+  if (a.E != 0 && a.E != 8) return cudaSuccess;
+  switch (a.M) {
+    case 64: return launch_tma_one<64, 8>(a, st, used);
+    case 128: return launch_tma_one<128, 8>(a, st, used);
+    case 256: return launch_tma_one<256, 8>(a, st, used);
+    case 512: return launch_tma_one<512, 8>(a, st, used);
+    default: return cudaSuccess;
+  }
+}
+
+}  // namespace gpe

@@ -46,6 +46,12 @@ static cudaError_t launch_pass_e4(int mode, Pass pass, const PassArgs& a, cudaSt
 
 cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
   if (a.E == 4) return launch_pass_e4(mode, pass, a, st);
+  if (mode == 0 && (pass == P_HMID || pass == P_HX)) {
+    // the passes of H phi through the TMA pipelines where the plan and the fields allow
+    bool used = false;
+    const cudaError_t e = pass == P_HMID ? launch_hmid_tma(a, st, &used) : launch_hx_bulk(a, st, &used);
+    if (e != cudaSuccess || used) return e;
+  }
   if (mode == 0) return launch_pass_f32(pass, a, st);
   if (mode == 1) return launch_pass_f64(pass, a, st);
   // refinement split: H phi and the state in double-single, the strided
