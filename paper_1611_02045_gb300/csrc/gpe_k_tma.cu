@@ -1,7 +1,8 @@
 // gpe_k_tma.cu -- the passes of H_phi f (Section 2 operator, eq. FFTdiscret of
 // Section 3) in complex64 fed by the Tensor Memory Accelerator:
-//  * y / z (role P_HMID): t += IFFT_axis[ (1/2 k^2 - omega x k) FFT_axis f ],
-//    the arithmetic of pass_s<float, M, P_HMID>, column tiles through 3D
+//  * y / z passes (roles P_HMID: t += IFFT_axis[ (1/2 k^2 - omega x k) FFT_axis f ];
+//    P_CFWD, P_CCORE, P_CINV: the Fourier core of P_C; P_AMID: the A p moments),
+//    the arithmetic of pass_s<float, M, ROLE>, column tiles through 3D
 //    tensor-map boxes;
 //  * x (role P_HX): t = IFFT_x[ (1/2 xi^2 + omega y xi) FFT_x f ] + (V + eta|phi|^2) f
 //    with the solver's retraction folded in, the arithmetic of
@@ -76,24 +77,32 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                : "memory");
 }
 
-template <int M, int EV>
-__global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_constant__ CUtensorMap tmf,
-                                                      const __grid_constant__ CUtensorMap tmt) {
+// Input tiles per unit of a strided role: f and t (H), s (the P_C passes), p (A p moments).
+template <int ROLE> struct STiles { static constexpr int value = ROLE == P_HMID ? 2 : 1; };
+
+template <int M, int EV, int ROLE>
+__global__ void __launch_bounds__(512) pass_s_tma(PassArgs a, const __grid_constant__ CUtensorMap tm0,
+                                                   const __grid_constant__ CUtensorMap tm1) {
   using T = float;
   using C = float2;
   constexpr int E = LineCfg<M, EV>::E, Tl = LineCfg<M, EV>::Tl;
   constexpr int BOX = M < 256 ? M : 256;  // rows per tensor-map box
   constexpr int NBOX = M / BOX;
+  constexpr int NT = STiles<ROLE>::value;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) unsigned long long bar[2];
-  if (a.solver && a.ctl->done) return;
+  if (a.solver && a.ctl->done) {
+    if (ROLE == P_AMID && a.last_axis && blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(a, 0);
+    return;
+  }
+  const Scal S = scal_of(a.ctl, a);
   const int tx = a.tx;
   const int tile = M * tx;  // elements of one column tile
-  C* stage = reinterpret_cast<C*>(smraw);  // [2 stages][f tile, t tile]
-  C* ex = stage + 4 * tile;                // transform exchange [M][tx]
+  C* stage = reinterpret_cast<C*>(smraw);  // [2 stages][NT tiles]
+  C* ex = stage + 2 * NT * tile;           // transform exchange [M][tx]
   const int c = threadIdx.x % tx, t = threadIdx.x / tx;
   const long long units = a.nblocks;
-  const unsigned bytes = 2u * (unsigned)tile * (unsigned)sizeof(C);
+  const unsigned bytes = (unsigned)NT * (unsigned)tile * (unsigned)sizeof(C);
 
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -102,12 +111,11 @@ __global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_co
   }
   __syncthreads();
 
-  // f and t columns of tile u into stage s (one thread)
+  // input columns of tile u into stage s (one thread)
   auto issue = [&](long long u, int s) {
     const int xt = (int)(u % a.ntx);
     const int outer = (int)(u / a.ntx);
-    C* fdst = stage + (2 * s) * tile;
-    C* tdst = fdst + tile;
+    C* d0 = stage + (NT * s) * tile;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stage's earlier generic reads
     mbar_expect_tx(&bar[s], bytes);
 #pragma unroll
@@ -115,8 +123,8 @@ __global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_co
       const int x0 = xt * tx;
       const int y0 = a.axis == 1 ? b * BOX : outer;
       const int z0 = a.axis == 1 ? outer : b * BOX;
-      tma_load_3d(fdst + b * BOX * tx, &tmf, x0, y0, z0, &bar[s]);
-      tma_load_3d(tdst + b * BOX * tx, &tmt, x0, y0, z0, &bar[s]);
+      tma_load_3d(d0 + b * BOX * tx, &tm0, x0, y0, z0, &bar[s]);
+      if constexpr (NT == 2) tma_load_3d(d0 + tile + b * BOX * tx, &tm1, x0, y0, z0, &bar[s]);
     }
   };
 
@@ -128,7 +136,6 @@ __global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_co
   const T invM = T(1) / T(M);
   const T om = T(a.omega);
   auto si = [tx, c](int pos) { return pos * tx + c; };
-  C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: the final pass writes the caller's buffer
 
   if (threadIdx.x == 0 && (long long)blockIdx.x < units) issue(blockIdx.x, 0);
   int i = 0;
@@ -149,38 +156,82 @@ __global__ void __launch_bounds__(512) pass_hmid_tma(PassArgs a, const __grid_co
       __syncthreads();
       break;
     }
-    const C* fs = stage + (2 * s) * tile;
-    const C* ts = fs + tile;
+    const C* in0 = stage + (NT * s) * tile;
     const int xt = (int)(u % a.ntx);
+    const long long outer = u / a.ntx;
     const int ix = xt * tx + c;
-    const long long base = (u / a.ntx) * a.outer_stride + ix;
-    C v[E], tv[E];
+    const long long base = outer * a.outer_stride + ix;
+    C v[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      v[q] = fs[(t + q * Tl) * tx + c];
-      tv[q] = ts[(t + q * Tl) * tx + c];
+    for (int q = 0; q < E; ++q) v[q] = in0[(t + q * Tl) * tx + c];
+    if constexpr (ROLE == P_HMID) {
+      // t += (1/2 mu^2 - omega x mu) f (y) or 1/2 zeta^2 f (z), the operand tile, then t
+      C tv[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) tv[q] = in0[tile + (t + q * Tl) * tx + c];
+      line_dft<M, E, -1>(v, ex, si, t, tw);
+      const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
+      const T rx = (a.axis == 1) ? -x : T(0);  // rotation symbol -omega x mu (y); none for z
+      T akin = 0, arot = 0;
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const T k = xia[t + q * Tl];
+        const T mk = T(0.5) * k * k, kr = rx * k;
+        const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
+        akin += mk * a2;
+        arot += kr * a2;
+        v[q] = cscale(v[q], (mk + om * kr) * invM);
+      }
+      line_dft<M, E, +1>(v, ex, si, t, tw);
+      C* __restrict__ dst = static_cast<C*>(a.out ? a.out : a.t);  // API: the final pass writes the caller's buffer
+#pragma unroll
+      for (int q = 0; q < E; ++q) dst[base + (t + q * Tl) * a.stride] = cadd(tv[q], v[q]);
+      acc[0] = acc_add(acc[0], acc_from(akin * invM));
+      acc[1] = acc_add(acc[1], acc_from(arot * invM));
+    } else if constexpr (ROLE == P_CFWD || ROLE == P_CINV || ROLE == P_CCORE) {
+      if constexpr (ROLE == P_CINV) {
+        line_dft<M, E, +1>(v, ex, si, t, tw);
+      } else {
+        line_dft<M, E, -1>(v, ex, si, t, tw);
+      }
+      if constexpr (ROLE == P_CCORE) {
+        // (alpha + |k|^2 / 2)^{-1} / N on the full frequency grid (eq. PDelta)
+        const T alpha = T(S.alpha);
+        const T invN = T(1.0 / ((double)a.nx * a.ny * (a.dim == 3 ? a.nz : 1)));
+        const T kx = tab<T>(a.xi[0])[ix];
+        T kother = 0;
+        if (a.dim == 3) {
+          const T ky = tab<T>(a.xi[1])[outer];  // axis 2 (z): the y index is the outer index
+          kother = ky * ky;
+        }
+        const bool core = pc_core(S.pc);
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const T k = xia[t + q * Tl];
+          const T den = alpha + T(0.5) * (kx * kx + kother + k * k);
+          v[q] = cscale(v[q], core ? invN / den : invN);
+        }
+        line_dft<M, E, +1>(v, ex, si, t, tw);
+      }
+      C* __restrict__ sb = static_cast<C*>(a.s);
+#pragma unroll
+      for (int q = 0; q < E; ++q) sb[base + (t + q * Tl) * a.stride] = v[q];
+    } else {
+      static_assert(ROLE == P_AMID, "strided roles: HMID, CFWD, CCORE, CINV, AMID");
+      line_dft<M, E, -1>(v, ex, si, t, tw);
+      const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
+      const T rs = (a.axis == 1) ? -om * x : T(0);
+      T akr = 0;
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const T k = xia[t + q * Tl];
+        akr += (T(0.5) * k * k + rs * k) * (v[q].x * v[q].x + v[q].y * v[q].y);
+      }
+      acc[0] = acc_add(acc[0], acc_from(akr * invM));
     }
-    line_dft<M, E, -1>(v, ex, si, t, tw);
-    const T x = (a.axis == 1) ? tab<T>(a.xc[0])[ix] : T(0);
-    const T rx = (a.axis == 1) ? -x : T(0);  // rotation symbol -omega x mu (y); none for z
-    T akin = 0, arot = 0;
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const T k = xia[t + q * Tl];
-      const T mk = T(0.5) * k * k, kr = rx * k;
-      const T a2 = v[q].x * v[q].x + v[q].y * v[q].y;
-      akin += mk * a2;
-      arot += kr * a2;
-      v[q] = cscale(v[q], (mk + om * kr) * invM);
-    }
-    line_dft<M, E, +1>(v, ex, si, t, tw);
-#pragma unroll
-    for (int q = 0; q < E; ++q) dst[base + (t + q * Tl) * a.stride] = cadd(tv[q], v[q]);
-    acc[0] = acc_add(acc[0], acc_from(akin * invM));
-    acc[1] = acc_add(acc[1], acc_from(arot * invM));
     __syncthreads();  // stage s is read by every thread before it is refilled
   }
-  reduce_and_finish<P_HMID>(a, acc);
+  reduce_and_finish<ROLE>(a, acc);
 }
 
 // x pass of H phi: blocks of lpb whole lines (rows), persistent over the units
@@ -345,28 +396,43 @@ bool encode_field(CUtensorMap* m, const void* base, const PassArgs& a, int box) 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int M, int EV>
-cudaError_t launch_tma_one(const PassArgs& a, cudaStream_t st, bool* used) {
+template <int M, int EV, int ROLE>
+cudaError_t launch_tma_one(const PassArgs& a0, cudaStream_t st, bool* used) {
   constexpr int Tl = LineCfg<M, EV>::Tl;
+  constexpr int NT = STiles<ROLE>::value;
+  PassArgs a = a0;
+  // tiles of at least 8 columns (64-byte row segments per box row) where the grid and
+  // the thread cap allow: narrower plans (tuned for the one-tile-per-block kernel)
+  // are widened; the tile count follows
+  if (a.tx < 8 && a.nx % 8 == 0 && Tl * 8 <= 512) {
+    const long long outer = a.nblocks / a.ntx;
+    a.tx = 8;
+    a.ntx = a.nx / 8;
+    a.nblocks = (int)(a.ntx * outer);
+  }
   const int threads = Tl * a.tx;
   if (threads > 512 || a.tx < 2 || (a.tx & 1)) return cudaSuccess;  // 16-byte rows: tx even
-  const size_t smem = (size_t)5 * M * a.tx * sizeof(float2);
+  const size_t smem = (size_t)(2 * NT + 1) * M * a.tx * sizeof(float2);
   if (smem > 200 * 1024) return cudaSuccess;
-  const void* fsrc = (a.f && !a.solver) ? a.f : a.phi;
-  if ((reinterpret_cast<uintptr_t>(fsrc) & 15u) || (reinterpret_cast<uintptr_t>(a.t) & 15u)) return cudaSuccess;
-  CUtensorMap tmf, tmt;
+  const void* src0 = ROLE == P_HMID ? ((a.f && !a.solver) ? a.f : a.phi) : (ROLE == P_AMID ? a.p : a.s);
+  const void* src1 = ROLE == P_HMID ? a.t : src0;
+  if ((reinterpret_cast<uintptr_t>(src0) & 15u) || (reinterpret_cast<uintptr_t>(src1) & 15u)) return cudaSuccess;
+  CUtensorMap tm0, tm1;
   constexpr int BOX = M < 256 ? M : 256;
-  if (!encode_field(&tmf, fsrc, a, BOX) || !encode_field(&tmt, a.t, a, BOX)) return cudaSuccess;
-  auto kern = pass_hmid_tma<M, EV>;
+  if (!encode_field(&tm0, src0, a, BOX)) return cudaSuccess;
+  if (NT == 2 && !encode_field(&tm1, src1, a, BOX)) return cudaSuccess;
+  if (NT == 1) tm1 = tm0;
+  auto kern = pass_s_tma<M, EV, ROLE>;
   static DeviceOnce attr;
-  static std::atomic<int> occ_dev[64][2];  // blocks per SM, per device and tx class (0 = unknown)
+  static std::atomic<int> occ_dev[64][8];  // blocks per SM, per device and tile width (log2 tx; 0 = unknown)
   const int dev = DeviceOnce::device();
   if (!attr.done(dev)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr.set(dev);
   }
-  const int cls = a.tx >= 8 ? 1 : 0;
+  int cls = 0;
+  while ((2 << cls) <= a.tx && cls < 7) ++cls;
   int occ = (dev >= 0 && dev < 64) ? occ_dev[dev][cls].load() : 0;
   if (occ <= 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
@@ -378,8 +444,19 @@ cudaError_t launch_tma_one(const PassArgs& a, cudaStream_t st, bool* used) {
   long long grid = (long long)occ * nsm;
   if (grid > a.nblocks) grid = a.nblocks;
   *used = true;
-  kern<<<(unsigned)grid, threads, smem, st>>>(a, tmf, tmt);
+  kern<<<(unsigned)grid, threads, smem, st>>>(a, tm0, tm1);
   return cudaGetLastError();
+}
+
+template <int ROLE>
+cudaError_t launch_s_role(const PassArgs& a, cudaStream_t st, bool* used) {
+  switch (a.M) {
+    case 64: return launch_tma_one<64, 8, ROLE>(a, st, used);
+    case 128: return launch_tma_one<128, 8, ROLE>(a, st, used);
+    case 256: return launch_tma_one<256, 8, ROLE>(a, st, used);
+    case 512: return launch_tma_one<512, 8, ROLE>(a, st, used);
+    default: return cudaSuccess;
+  }
 }
 
 template <int M, int EV>
@@ -443,18 +520,19 @@ cudaError_t launch_hx_bulk(const PassArgs& a, cudaStream_t st, bool* used) {
   }
 }
 
-// y / z pass of H phi in complex64 through the TMA pipeline when the plan and
-// the fields allow it (E = 8, even tile width, 16-byte aligned f and t,
-// M in {64, 128, 256, 512}); *used = false otherwise (the caller launches
-// pass_s).
-cudaError_t launch_hmid_tma(const PassArgs& a, cudaStream_t st, bool* used) {
+// A strided pass (y or z) in complex64 through the TMA pipeline when the plan
+// and the fields allow it (E = 8, even tile width, 16-byte aligned inputs,
+// M in {64, 128, 256, 512}); roles P_HMID, P_CFWD, P_CCORE, P_CINV, P_AMID;
+// *used = false otherwise (the caller launches pass_s).
+cudaError_t launch_strided_tma(Pass pass, const PassArgs& a, cudaStream_t st, bool* used) {
   *used = false;
   if (a.E != 0 && a.E != 8) return cudaSuccess;
-  switch (a.M) {
-    case 64: return launch_tma_one<64, 8>(a, st, used);
-    case 128: return launch_tma_one<128, 8>(a, st, used);
-    case 256: return launch_tma_one<256, 8>(a, st, used);
-    case 512: return launch_tma_one<512, 8>(a, st, used);
+  switch (pass) {
+    case P_HMID: return launch_s_role<P_HMID>(a, st, used);
+    case P_CFWD: return launch_s_role<P_CFWD>(a, st, used);
+    case P_CCORE: return launch_s_role<P_CCORE>(a, st, used);
+    case P_CINV: return launch_s_role<P_CINV>(a, st, used);
+    case P_AMID: return launch_s_role<P_AMID>(a, st, used);
     default: return cudaSuccess;
   }
 }
