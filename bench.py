@@ -113,6 +113,9 @@ def parse():
                     help="skip the sweep's instances solved one at a time in FP64")
     ap.add_argument("--no-grad", action="store_true", help="skip the 16-instance differentiation workload")
     ap.add_argument("--no-paper", action="store_true", help="skip the 512^2 solves of the paper's Tables 2 and 3")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 legs (accuracy against the FP64 solve, the FP64 roof, the pipe rates)")
+    ap.add_argument("--no-fftpass", action="store_true", help="skip H phi on the 256x256x512 field (pass bandwidth)")
     ap.add_argument("--no-libfft", action="store_true",
                     help="skip the library-FFT baseline (torch.fft / cuFFT complex128 PCG_C) and the FP64 solve")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pass-kernel plans")
@@ -419,9 +422,10 @@ def main():
     # field (268 MB in, 268 MB out), flops by the nominal 5 M log2 M model per line transform
     # (3 axes x forward + inverse) plus 20 flops per point for the multipliers and the real-space
     # term, against the measured FP64 fma rate.
-    alu = {k: gpe.alu_peak(k) for k in ("fp64_fma", "fp32_fma", "fp32x2_fma")}
-    fp64_roof = None
-    if rank == 0:
+    alu, fp64_roof = None, None
+    if not args.no_fp64:
+        alu = {k: gpe.alu_peak(k) for k in ("fp64_fma", "fp32_fma", "fp32x2_fma")}
+    if rank == 0 and not args.no_fp64:
         n3, L3 = (256, 256, 256), (8.0, 8.0, 8.0)
         N3 = int(np.prod(n3))
         with gpe.Context(n3, L3, 5000.0, 0.8, I.harmonic(n3, L3, [1.0, 1.0, 2.0]), prec=gpe.GPE_FP64) as c3:
@@ -447,6 +451,38 @@ def main():
                      "ms_per_call": ms3, "hbm_gbs_algorithmic": 40.0 * N3 / (ms3 * 1e-3) / 1e9,
                      "flop_model": "5 M log2 M per line transform x 6 transforms + 20 per point",
                      "peak_source": "gpe_alu_peak(fp64 fma), measured in this run"}
+
+    # ---------------- H phi on one 256x256x512 complex64 field (beyond L2): the pass kernels ----------------
+    # gpe_apply_H = x pass (phi, V in; t out), y and z passes (f, t in; t / H phi out), each a
+    # TMA-fed persistent kernel; algorithmic bytes 20 per point for the operator (read phi and V,
+    # write H phi) and 68 per point summed over the three passes (20 + 24 + 24).  Per-pass DRAM figures: the ncu
+    # summary profiles/fft_passes_256x256x512_c64.md.
+    fftpass = None
+    if rank == 0 and not args.no_fftpass:
+        nf3, Lf3 = (256, 256, 512), (8.0, 8.0, 8.0)
+        Nf3 = int(np.prod(nf3))
+        with gpe.Context(nf3, Lf3, 100.0, 0.5, np.zeros(I.shape_of(nf3)), prec=gpe.GPE_MIXED) as cf3:
+            gf = torch.Generator(device=dev).manual_seed(5)
+            xf = torch.randn(Nf3, dtype=torch.complex64, device=dev, generator=gf)
+            yf = torch.empty_like(xf)
+            for _ in range(3):
+                cf3.apply_H(xf, xf, yf)
+            tf = []
+            for _ in range(10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cf3.apply_H(xf, xf, yf)
+                b.record(stream)
+                b.synchronize()
+                tf.append(a.elapsed_time(b))
+            del xf, yf
+        msf = statistics.median(tf)
+        fftpass = {"field": "256x256x512 complex64 (268 MB)", "ms_per_call": msf,
+                   "operator_gbs": 20.0 * Nf3 / (msf * 1e-3) / 1e9,
+                   "passes_gbs": 68.0 * Nf3 / (msf * 1e-3) / 1e9,
+                   "passes_frac": 68.0 * Nf3 / (msf * 1e-3) / 1e9 / peak,
+                   "kernels": "pass_hx_bulk<256,8>, pass_s_tma<256,8,HMID>, pass_s_tma<512,8,HMID>",
+                   "per_pass": "profiles/fft_passes_256x256x512_c64.md"}
 
     # ---------------- secondary: the 128^3 workload ----------------
     secondary = None
@@ -637,7 +673,7 @@ def main():
         return out, a.elapsed_time(b)
 
     accuracy, fp64_solve = None, None
-    if rank == 0:
+    if rank == 0 and not args.no_fp64:
         ctx64 = gpe.Context(n, L, w["eta"], w["omega"], w["V"], prec=gpe.GPE_FP64)
         if not args.no_autotune:
             ctx64.autotune(iters=10)
@@ -730,6 +766,7 @@ def main():
             "clocks": clk,
             "accuracy": accuracy,
             "alu_peaks_gflops": alu,
+            "fft_passes": fftpass,
             "fp64_roofline": fp64_roof,
             "cpu_baseline": cpu,
             "secondary": secondary,

@@ -141,12 +141,14 @@ cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st)
 // The y / z passes in complex64 (roles P_HMID, P_CFWD, P_CCORE, P_CINV,
 // P_AMID) fed by tensor-map (TMA) tile loads in a persistent, double-buffered
 // kernel (gpe_k_tma.cu); *used = false when the plan or the fields do not
-// allow it (E = 8, even tile width, 16-byte aligned inputs): the caller then
-// launches the standard pass kernel.
+// allow it (E = 8, even tile width, 16-byte aligned inputs) or the field is
+// too small for every block to get two tiles: the caller then launches the
+// standard pass kernel.
 cudaError_t launch_strided_tma(Pass pass, const PassArgs& a, cudaStream_t st, bool* used);
 // The x pass of H phi in complex64 fed by 1D bulk copies (phi, f or p, V rows)
 // in a persistent, double-buffered kernel (gpe_k_tma.cu); *used = false when
-// it does not apply (E = 8, M in 64 .. 512, 16-byte aligned fields).
+// it does not apply (E = 8, M in 64 .. 512, 16-byte aligned fields, at least
+// two units per block).
 cudaError_t launch_hx_bulk(const PassArgs& a, cudaStream_t st, bool* used);
 
 // Per-group launchers (gpe_k_<prec>_<group>.cu).

@@ -441,8 +441,10 @@ cudaError_t launch_tma_one(const PassArgs& a0, cudaStream_t st, bool* used) {
   }
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaGetLastError();
-  long long grid = (long long)occ * nsm;
-  if (grid > a.nblocks) grid = a.nblocks;
+  const long long grid = (long long)occ * nsm;
+  // the pipeline pays when every block has at least two tiles to overlap; smaller
+  // fields (L2-resident 2D grids) keep the tuned one-tile-per-block kernel
+  if (a.nblocks < 2 * grid) return cudaSuccess;
   *used = true;
   kern<<<(unsigned)grid, threads, smem, st>>>(a, tm0, tm1);
   return cudaGetLastError();
@@ -496,8 +498,8 @@ cudaError_t launch_hx_one(const PassArgs& a0, cudaStream_t st, bool* used) {
   }
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaGetLastError();
-  long long grid = (long long)occ * nsm;
-  if (grid > a.nblocks) grid = a.nblocks;
+  const long long grid = (long long)occ * nsm;
+  if (a.nblocks < 2 * grid) return cudaSuccess;  // at least two units per block, as for the strided passes
   *used = true;
   kern<<<(unsigned)grid, threads, smem, st>>>(a, second);
   return cudaGetLastError();

@@ -85,6 +85,48 @@ __device__ __forceinline__ Acc red_op(Acc a, Acc b, int k) {
   return ((MAXMASK >> k) & 1u) ? acc_max(a, b) : acc_add(a, b);
 }
 
+// Two double-single additions at once on the packed two-wide FP32 pipe: lane by
+// lane the same operations in the same order as acc_add (each lane rounds like
+// the scalar .rn operation), so the sums are bit-identical with half the
+// floating-point instructions.
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ void acc_add2(Acc& a0, Acc& a1, Acc b0, Acc b1) {
+  const unsigned long long ah = f2_pack(a0.hi, a1.hi), al = f2_pack(a0.lo, a1.lo);
+  const unsigned long long bh = f2_pack(b0.hi, b1.hi), bl = f2_pack(b0.lo, b1.lo);
+  const unsigned long long sm = f2add(ah, bh);
+  const unsigned long long bp = f2sub(sm, ah);
+  unsigned long long e = f2add(f2sub(ah, f2sub(sm, bp)), f2sub(bh, bp));
+  e = f2add(e, f2add(al, bl));
+  const unsigned long long h = f2add(sm, e);
+  const unsigned long long lo = f2sub(e, f2sub(h, sm));
+  const float2 H = f2_unpack(h), Lo = f2_unpack(lo);
+  a0 = Acc{H.x, Lo.x};
+  a1 = Acc{H.y, Lo.y};
+}
+
+// v[k] = red_op(v[k], w[k]) for every slot; pairs of sum slots go through acc_add2.
+template <int K, unsigned MAXMASK>
+__device__ __forceinline__ void red_all(Acc (&v)[K], const Acc (&w)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    if (k + 1 < K && !((MAXMASK >> k) & 1u) && !((MAXMASK >> (k + 1)) & 1u)) {
+      acc_add2(v[k], v[k + 1], w[k], w[k + 1]);
+    } else {
+      v[k] = red_op<MAXMASK>(v[k], w[k], k);
+      if (k + 1 < K) v[k + 1] = red_op<MAXMASK>(v[k + 1], w[k + 1], k + 1);
+    }
+  }
+}
+
 __device__ __forceinline__ Acc shfl_acc(unsigned mask, Acc v, int o) {
   return Acc{__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o)};
 }
@@ -95,8 +137,10 @@ template <int K, unsigned MAXMASK>
 __device__ __forceinline__ void warp_tree(Acc (&v)[K]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
+    Acc w[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = red_op<MAXMASK>(v[k], shfl_acc(0xffffffffu, v[k], o), k);
+    for (int k = 0; k < K; ++k) w[k] = shfl_acc(0xffffffffu, v[k], o);
+    red_all<K, MAXMASK>(v, w);
   }
 }
 
@@ -112,8 +156,10 @@ __device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     if (o < width) {
+      Acc w[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = red_op<MAXMASK>(v[k], shfl_acc(mask, v[k], o), k);
+      for (int k = 0; k < K; ++k) w[k] = shfl_acc(mask, v[k], o);
+      red_all<K, MAXMASK>(v, w);
     }
   }
   if (nw == 1) return;
