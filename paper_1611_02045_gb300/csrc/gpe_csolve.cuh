@@ -104,16 +104,19 @@ __device__ __forceinline__ void cs_yunit(const cgc::cluster_group& cl, int rank,
 }
 
 // Cluster-wide fixed-order sum of the CTAs' block totals (tot[] in FP64,
-// valid in every thread of every CTA on return).  part[2][C][kMaxMoments]
-// lives in CTA 0's shared memory; parity alternates between reductions so a
-// slow reader never sees the next reduction's partials.
+// valid in thread 0 of every CTA on return: only thread 0 runs the scalar
+// steps).  part[2][C][kMaxMoments] lives in CTA 0's shared memory and red_sm
+// holds two block buffers; parity alternates between reductions, so a slow
+// reader never sees the next reduction's partials, and the cluster barrier of
+// the reduction in between orders a buffer's readers before its next writers:
+// no block barrier before the block sum and none after the cluster sum.
 template <int K, unsigned MAXMASK>
 __device__ __forceinline__ void cs_reduce(const cgc::cluster_group& cl, int rank, int csize, const Acc* acc,
                                           Acc* part, int& parity, Acc* red_sm, double* tot) {
   Acc v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = acc[k];
-  block_reduce<K, MAXMASK>(v, red_sm);
+  block_reduce<K, MAXMASK, false>(v, red_sm + parity * 32 * kMaxMoments);
   Acc* p0 = cl.map_shared_rank(part, 0u) + (size_t)parity * kCSRows * kMaxMoments;
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -131,7 +134,6 @@ __device__ __forceinline__ void cs_reduce(const cgc::cluster_group& cl, int rank
       for (int k = 0; k < K; ++k) tot[k] = acc_to_double(v[k]);
     }
   }
-  __syncthreads();
   parity ^= 1;
 }
 
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__((M / 8) * kCSRows) cluster_solve(ClusterSolveA
   float2* xs = r_s + R * M;  // exchange scratch, R * LS elements
   __shared__ Ctl S;
   __shared__ Acc part[2 * kCSRows * kMaxMoments];
-  __shared__ Acc red_sm[32 * kMaxMoments];
+  __shared__ Acc red_sm[2 * 32 * kMaxMoments];  // two buffers, alternating with the reductions
   __shared__ double tot[kMaxMoments];
 
   const int row0 = rank * R;

@@ -147,7 +147,10 @@ __device__ __forceinline__ void warp_tree(Acc (&v)[K]) {
 // Block total of v[k] (fixed tree); valid in thread 0 on return.  Warp sums
 // by shuffles, then warp 0 combines the per-warp sums with a second shuffle
 // tree (no serial loop over warps).
-template <int K, unsigned MAXMASK>
+// LEAD = false skips the barrier that protects red_sm from the previous call's
+// readers: for callers that alternate between two red_sm buffers, whose other
+// barriers already order a buffer's readers before its next writers.
+template <int K, unsigned MAXMASK, bool LEAD = true>
 __device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
   // blockDim.x is a power of two: either a multiple of 32 or one partial warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -163,7 +166,7 @@ __device__ __forceinline__ void block_reduce(Acc (&v)[K], Acc* red_sm) {
     }
   }
   if (nw == 1) return;
-  __syncthreads();
+  if constexpr (LEAD) __syncthreads();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) red_sm[warp * K + k] = v[k];
