@@ -53,7 +53,8 @@ __device__ __forceinline__ void cs_yunit(const cgc::cluster_group& cl, int rank,
     w[q] = src[(y % R) * M + x];
   }
   auto si = [c](int pos) { return pos * R + c; };
-  line_dft<M, E, -1>(w, xs, si, t, tw);
+  // the last users of xs were the x unit before the reduction's cluster barrier
+  line_dft<M, E, -1, false, false>(w, xs, si, t, tw);
   if constexpr (ROLE == P_HMID || ROLE == P_AMID) {
     const float om = float(a.omega);
     const float rx = -static_cast<const float*>(a.xc[0])[x];

@@ -163,7 +163,10 @@ template <bool WARP> __device__ __forceinline__ void line_sync() {
 // Stockham stages.  SI: functor mapping a line position to a shared-memory
 // element index for this thread's line slot.
 // ---------------------------------------------------------------------------
-template <int M, int E, int NS, int DIR, bool WARP, typename C, typename SI>
+// LEAD = false: the caller guarantees that no thread still reads sm (a block or
+// cluster barrier since its last use), so the first exchange needs no barrier
+// before its stores.
+template <int M, int E, int NS, int DIR, bool WARP, bool LEAD = true, typename C, typename SI>
 __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
   constexpr int Tl = M / E;
   constexpr int R = (M / NS >= E) ? E : (M / NS);
@@ -184,7 +187,7 @@ __device__ __forceinline__ void fft_stages(C (&v)[E], C* sm, const SI& si, int t
     for (int r = 0; r < R; ++r) v[b + r * NB] = x[r];
   }
   if constexpr (NS * R < M) {
-    line_sync<WARP>();  // previous readers of sm are done
+    if constexpr (LEAD || NS > 1) line_sync<WARP>();  // previous readers of sm are done
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = t + b * Tl;
@@ -250,9 +253,9 @@ __device__ __forceinline__ void dft256x16(float2 (&v)[16], float2* sm, const SI&
 // Forward (DIR = -1) or inverse-unnormalised (DIR = +1) DFT of one line held
 // as v[q] = f[t + q*Tl]; on return v[q] = F[f][t + q*Tl].  Every thread of the
 // block (WARP: of the warp) must call it: it contains the stage barriers.
-template <int M, int E, int DIR, bool WARP = false, typename C, typename SI>
+template <int M, int E, int DIR, bool WARP = false, bool LEAD = true, typename C, typename SI>
 __device__ __forceinline__ void line_dft(C (&v)[E], C* sm, const SI& si, int t, const C* __restrict__ tw) {
-  fft_stages<M, E, 1, DIR, WARP>(v, sm, si, t, tw);
+  fft_stages<M, E, 1, DIR, WARP, LEAD>(v, sm, si, t, tw);
 }
 
 }  // namespace gpe
