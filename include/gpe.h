@@ -180,17 +180,26 @@ gpe_status gpe_apply_H(gpe_ctx* ctx, const void* phi_dev, const void* f_dev, voi
 /* out_b = H_{phi_b} f_b for b = 0 .. nbatch-1 (the operator of gpe_apply_H,
  * Section 2 / eq. FFTdiscret), on nbatch fields stored one after another
  * (stride nx*ny elements), all with the context's V, eta and omega.  2D
- * contexts with nx == ny in [32, 256] only.  Each field is transformed by one
- * thread-block cluster (16 rows per CTA) in distributed shared memory, so
- * global memory is read and written once per point (the output is written by
- * the row phase and completed by the column phase while still in L2).  In
- * single precision with n >= 64 and 16-byte aligned phi and f, the resident
- * clusters loop over the fields and copy the next field's rows while
- * transforming the current one (plan mode 3 of gpe_set_plan: E = 16, the
- * default, with 16 or 32 rows per CTA; E = 8 selects one field per cluster).  phi_dev, f_dev, out_dev:
- * device arrays in working precision; f may equal phi; out must not overlap
- * phi or f.  Asynchronous.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other
- * grids), GPE_ERR_CUDA. */
+ * contexts with nx == ny in [32, 256] only.  Global memory is read and written
+ * once per point (the output is written by the row part and completed by the
+ * column part while still in L2).  Forms, by plan mode 3 of gpe_set_plan:
+ *  - single precision, 256 x 256, f == phi, 16-byte aligned fields and V,
+ *    E = 16 with width 16 (the default): a dataflow of row units and column
+ *    units (16 lines each) taken by persistent blocks on every SM from one
+ *    ticket queue, inputs copied by the TMA; a field's column units add their
+ *    part after its row units have stored theirs.  Uses a counter array of the
+ *    context (nbatch + 2 ints, allocated on first use and when the batch
+ *    grows; zero between calls), so one such call runs at a time per context;
+ *  - otherwise one thread-block cluster per field (16 rows per CTA) in
+ *    distributed shared memory; in single precision with n >= 64 and 16-byte
+ *    aligned phi and f the resident clusters loop over the fields and copy the
+ *    next field's rows while transforming the current one (E = 16, 16 or 32
+ *    rows per CTA; E = 8 selects one field per cluster).
+ * phi_dev, f_dev, out_dev: device arrays in working precision; f may equal
+ * phi; out must not overlap phi or f.  Asynchronous.  A bounded wait of the
+ * dataflow form that gives up (never expected) marks the context's API status
+ * GPE_ERR_TIMEOUT.  Errors: GPE_ERR_ARG, GPE_ERR_UNSUPPORTED (other grids),
+ * GPE_ERR_CUDA. */
 gpe_status gpe_apply_H_batch(gpe_ctx* ctx, int nbatch, const void* phi_dev, const void* f_dev, void* out_dev);
 
 /* out = P_C r = P_V^{1/2} P_Delta P_V^{1/2} r (eq. combinedP_12) with
@@ -391,10 +400,10 @@ gpe_status gpe_autotune(gpe_ctx* ctx, int iters, int use_cache, gpe_tune_report*
  * cannot run (E not 4 or 8, E = 4 below M = 32, width not a power of two, more
  * threads than the mode's kernels allow, too much shared memory, more blocks
  * than the context's reduction buffers) with GPE_ERR_ARG.  Mode 3, axis 0 is
- * the cluster kernel of gpe_apply_H_batch: E = 8 (one field per cluster, 16
- * rows per CTA) or E = 16 (the streaming form, single precision, n >= 64)
- * with width = rows per CTA, 16 (a cluster of n/16 CTAs) or 32 (n/32 CTAs,
- * so an 8-CTA cluster at n = 256). */
+ * the kernel of gpe_apply_H_batch: E = 8 (one field per cluster, 16 rows per
+ * CTA) or E = 16 (single precision, n >= 64) with width 16 (the dataflow form
+ * where it applies, else the streaming form with a cluster of n/16 CTAs) or
+ * 32 (the streaming form with n/32 CTAs, so an 8-CTA cluster at n = 256). */
 gpe_status gpe_set_plan(gpe_ctx* ctx, int mode, int axis, int E, int width);
 /* The plan in use for (mode, axis): *E values per thread and *width (lines per
  * block on axis 0, tile columns on the others; rows per CTA for mode 3), host

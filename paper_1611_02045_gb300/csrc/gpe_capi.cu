@@ -71,6 +71,8 @@ struct gpe_ctx {
   PassPlan mplan[3][3];  // plan used per launch mode [mode][axis] (the default, or the tuner's choice)
   int partials_cap = 0;  // blocks the reduction partials buffer holds
   int hbatch_rows = 16;  // rows per CTA of its streaming form (plan mode 3 width: 16 or 32)
+  int* hflow_ctr = nullptr;  // counters of gpe_apply_H_batch's dataflow form (zero between launches)
+  int hflow_cap = 0;
   int hbatch_E = 8;      // values per thread of gpe_apply_H_batch's cluster kernel (plan mode 3):
                          // 16 (streaming form) by default in single precision for n >= 64
   double vmax = 0.0;  // max V on the grid
@@ -273,6 +275,7 @@ static void free_ctx(gpe_ctx* c) {
   for (auto& a : c->adj) cudaFree(a);
   cudaFree(c->tf_state);
   cudaFree(c->adj_s); cudaFree(c->adj_partials);
+  cudaFree(c->hflow_ctr);
   cudaFree(c->ctl_solve); cudaFree(c->ctl_api); cudaFree(c->partials); cudaFree(c->ticket); cudaFree(c->log_dev);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
@@ -421,6 +424,23 @@ extern "C" gpe_status gpe_apply_H_batch(gpe_ctx* c, int nbatch, const void* phi,
   a.phi = phi; a.f = f; a.out = out;
   a.E = c->hbatch_E;
   a.rows = c->hbatch_rows;
+  if (prec == 0 && a.M == 256 && a.E == 16 && a.rows == 16 && phi == f) {
+    // the dataflow form's counters: allocated (zeroed) on first use and when the batch grows;
+    // the kernel leaves them zero
+    const size_t need = h_batch_flow_counters(nbatch);
+    if ((size_t)c->hflow_cap < need) {
+      const size_t cap = need > 2 * (size_t)c->hflow_cap ? need : 2 * (size_t)c->hflow_cap;
+      if (c->hflow_ctr) GPE_CU(c, cudaFree(c->hflow_ctr));
+      c->hflow_ctr = nullptr;
+      c->hflow_cap = 0;
+      GPE_CU(c, cudaMalloc(&c->hflow_ctr, cap * sizeof(int)));
+      GPE_CU(c, cudaMemsetAsync(c->hflow_ctr, 0, cap * sizeof(int), c->st));
+      c->hflow_cap = (int)cap;
+    }
+    a.flow_ctr = c->hflow_ctr;
+    a.flow_cap = c->hflow_cap;
+    a.status = &c->ctl_api->status;
+  }
   GPE_CU(c, launch_cluster_apply_H(prec, a, c->st));
   return GPE_OK;
 }

@@ -14,6 +14,12 @@ cudaError_t launch_cluster_apply_H(int is_double, const ClusterHArgs& a, cudaStr
       default: return cudaErrorInvalidValue;
     }
   }
+  if (a.E == 16 && a.rows != 32 && a.M == 256) {
+    // single precision, E = 16, 256 x 256 fields with f == phi: the dataflow form
+    bool used = false;
+    const cudaError_t e = launch_h_batch_flow(a, a.flow_ctr, a.flow_cap, a.status, st, &used);
+    if (e != cudaSuccess || used) return e;
+  }
   if (a.E == 16) {
     // single precision, E = 16: the streaming (persistent, prefetching) form
     // when the fields are 16-byte aligned, else one field per cluster

@@ -41,7 +41,17 @@ struct ClusterHArgs {
   void* out;         // results
   int E;             // values per thread: 16 (single precision, M >= 64) or 8 (also when 0)
   int rows;          // streaming form (E = 16): rows per CTA, 16 (also when 0) or 32
+  int* flow_ctr;     // dataflow form (gpe_hflow.cu): zeroed counters, at least nbatch + 2 ints (or null)
+  int flow_cap;      // ints in flow_ctr
+  int* status;       // device int set to GPE_ERR_TIMEOUT when a bounded wait gives up (or null)
 };
+
+// The dataflow form of the batched H phi for 256 x 256 complex64 fields with
+// f == phi (gpe_hflow.cu); *used = false when the call does not qualify (the
+// caller then launches a cluster form).
+cudaError_t launch_h_batch_flow(const ClusterHArgs& a, int* ctr, int ctr_cap, int* status, cudaStream_t st,
+                                bool* used);
+size_t h_batch_flow_counters(int nbatch);
 
 // Two CTAs per SM in single precision (two fields in flight per SM group).
 template <typename T> struct ClusterMinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };

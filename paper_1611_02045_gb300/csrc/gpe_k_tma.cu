@@ -27,55 +27,11 @@
 #include <mutex>
 
 #include "gpe_passes.cuh"
+#include "gpe_tma.cuh"
 
 namespace gpe {
 
 namespace {
-
-constexpr long long kTmaWaitLimit = 1ll << 24;  // try_wait polls (each may suspend briefly): seconds
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// true when the phase with the given parity has completed; false after the bound.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  const unsigned a = smem_u32(bar);
-  for (long long n = 0; n < kTmaWaitLimit; ++n) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// 3D tile load global -> shared through the tensor map, completing on bar.
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
-        "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Contiguous global -> shared bulk copy (16-byte aligned, size a multiple of 16),
-// completing on bar.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 // Input tiles per unit of a strided role: f and t (H), s (the P_C passes), p (A p moments).
 template <int ROLE> struct STiles { static constexpr int value = ROLE == P_HMID ? 2 : 1; };
@@ -367,21 +323,6 @@ __global__ void __launch_bounds__(512) pass_hx_bulk(PassArgs a, int second) {
   reduce_and_finish<P_HX>(a, acc);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 // Tensor map over a complex64 field [nz][ny][nx] (8-byte elements), boxes of
 // tx x-columns along the pass axis (BOX rows).
 bool encode_field(CUtensorMap* m, const void* base, const PassArgs& a, int box) {
@@ -506,6 +447,22 @@ cudaError_t launch_hx_one(const PassArgs& a0, cudaStream_t st, bool* used) {
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
 
 // x pass of H phi in complex64 through the bulk-copy pipeline (M in 64 .. 512,
 // 16-byte aligned phi, f or p and V, E = 8); *used = false otherwise.

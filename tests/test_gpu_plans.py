@@ -255,3 +255,81 @@ def test_batched_H_kernel_falls_back_for_misaligned_fields(G):
     fh = host(f_d).reshape(nb, M, M)
     for b in range(nb):
         assert relmax(got[b], O.apply_H(po, fh[b], fh[b])) < 2e-5, b
+
+
+def _flow_fields(nb, seed0, n, L):
+    return np.stack([I.random_field(seed0 + b, n, L) for b in range(nb)])
+
+
+def test_dataflow_batched_H_matches_oracle_ragged_batches(G):
+    """The dataflow form of gpe_apply_H_batch (256 x 256 complex64, f == phi:
+    row and column units from one ticket queue, column units waiting on the
+    field's row-unit counter, TMA-fed stages, TMA reduce-add of the column
+    part) against the oracle, field by field, on batches below, at and above
+    the 32-field lag between a field's row and column units (1, 5, 32, 33, 70
+    fields), each batch twice and in an order that grows and shrinks the batch
+    (the kernel leaves its counters zero for the next launch)."""
+    M = 256
+    n, L = (M, M), (16.0, 16.0)
+    V = I.harmonic(n, L) + 0.3 * I.smooth_bumps(n, L, 4)
+    eta, om = 900.0, 0.85
+    po = O.Problem(n, L, eta, om, V)
+    fields = _flow_fields(70, 700, n, L)
+    with G.Context(n, L, eta, om, V, prec=G.GPE_MIXED) as ctx:
+        assert ctx.get_plan(3, 0) == (16, 16)
+        for nb in (5, 70, 1, 33, 32, 70):
+            f_d = dev(fields[:nb], torch.complex64)
+            out = torch.full_like(f_d, float("nan"))
+            for rep in range(2):
+                if rep:
+                    out.fill_(float("nan"))
+                ctx.apply_H_batch(nb, f_d, f_d, out)
+                got = host(out)
+                assert np.isfinite(got).all(), (nb, rep)
+            fh = host(f_d)
+            for b in range(nb):
+                assert relmax(got[b], O.apply_H(po, fh[b], fh[b])) < 2e-5, (nb, b)
+
+
+def test_dataflow_batched_H_full_size_sampled(G):
+    """The roofline launch of the benchmark: 512 fields of 256 x 256 complex64
+    (268 MB in, 268 MB out, above the 129 MB L2), f == phi, random normal
+    fields; sampled fields (first, around the lag, middle, last) against the
+    oracle, and every field finite."""
+    M, nb = 256, 512
+    n, L = (M, M), (16.0, 16.0)
+    V = I.harmonic(n, L)
+    eta, om = 1000.0, 0.9
+    po = O.Problem(n, L, eta, om, V)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(nb * M * M, dtype=torch.complex64, device="cuda", generator=g)
+    out = torch.empty_like(x)
+    with G.Context(n, L, eta, om, V, prec=G.GPE_MIXED) as ctx:
+        ctx.apply_H_batch(nb, x, x, out)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(torch.view_as_real(out)).all())
+        xs, os_ = x.view(nb, M, M), out.view(nb, M, M)
+        for b in (0, 31, 32, 33, 255, 480, 511):
+            fh = xs[b].cpu().numpy()
+            assert relmax(os_[b].cpu().numpy(), O.apply_H(po, fh, fh)) < 2e-5, b
+
+
+def test_dataflow_batched_H_falls_back_for_misaligned_fields(G):
+    """256 x 256 fields 8 bytes off a 16-byte boundary cannot be fed to the
+    TMA: the cluster form runs instead, with the same results."""
+    M, nb = 256, 4
+    n, L = (M, M), (16.0, 16.0)
+    V = I.harmonic(n, L)
+    po = O.Problem(n, L, 500.0, 0.5, V)
+    fs = _flow_fields(nb, 900, n, L)
+    buf = torch.empty(nb * M * M + 1, dtype=torch.complex64, device="cuda")
+    f_d = buf[1:]
+    f_d.copy_(torch.from_numpy(fs.reshape(-1).astype(np.complex64)))
+    assert f_d.data_ptr() % 16 == 8
+    out = torch.empty_like(f_d)
+    with G.Context(n, L, 500.0, 0.5, V, prec=G.GPE_MIXED) as ctx:
+        ctx.apply_H_batch(nb, f_d, f_d, out)
+        got = host(out).reshape(nb, M, M)
+    fh = host(f_d).reshape(nb, M, M)
+    for b in range(nb):
+        assert relmax(got[b], O.apply_H(po, fh[b], fh[b])) < 2e-5, b
