@@ -59,7 +59,7 @@ HPHI_BATCH = 512  # fields of 256x256 complex64 in the H phi roofline batch (268
 # ncu summary of the roofline kernel; its line "dram_bytes_per_launch_512_fields: <int>" holds
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch over HPHI_BATCH fields, taken from a
 # capture of the current kernel (the line is removed when the kernel changes).
-HPHI_PROFILE = os.path.join(ROOT, "profiles", "cluster_apply_H_stream_256x256_batch_c64.md")
+HPHI_PROFILE = os.path.join(ROOT, "profiles", "h_batch_flow_256x256_batch_c64.md")
 ORACLE_ITERATIONS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 
 
@@ -387,8 +387,8 @@ def main():
     e2e_val = job_throughput(max_over_ranks(statistics.mean(e2e_ms), dev), world)
 
     # ---------------- roofline: H phi on a batch of fields larger than L2 ----------------
-    # HPHI_BATCH fields of the workload's grid (gpe_apply_H_batch: resident 16-CTA clusters
-    # streaming over the fields), complex64: algorithmic bytes = read phi + write H phi
+    # HPHI_BATCH fields of the workload's grid (gpe_apply_H_batch: the dataflow of row and
+    # column units on every SM), complex64: algorithmic bytes = read phi + write H phi
     # per point (16 B) + V once (4 B per grid point, shared by the batch).
     NB = HPHI_BATCH
     g = torch.Generator(device=dev).manual_seed(1)
@@ -757,8 +757,9 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": hphi_traffic(),
                          "traffic_source": os.path.relpath(HPHI_PROFILE, ROOT),
-                         "kernel": "cluster_apply_H_stream<float,256,16> (gpe_apply_H_batch: resident 16-CTA "
-                                   "clusters looping over the fields, next rows prefetched)",
+                         "kernel": "h_batch_flow (gpe_apply_H_batch: row and column units of 16 lines from one "
+                                   "ticket queue on persistent blocks, TMA-fed stages, TMA reduce-add of the "
+                                   "column part)",
                          "grid": f"{NB} x 256x256", "bytes_per_launch": hbytes,
                          "ms_per_launch": h_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
