@@ -49,7 +49,8 @@ namespace {
 constexpr int kFM = 256;                                    // grid side
 constexpr size_t kFlowStage = 48 * 1024;                    // bytes per stage
 constexpr size_t kFlowTws = 16 * kTw256Stride * sizeof(float4);
-constexpr size_t kFlowSmem = 2 * kFlowStage + kFlowTws + 32;  // + 2 mbarriers, 2 unit ids
+constexpr size_t kFlowKt = 2 * kFM * sizeof(float2);          // multiplier tables (x, y)
+constexpr size_t kFlowSmem = 2 * kFlowStage + kFlowTws + kFlowKt + 32;  // + 2 mbarriers, 2 unit ids
 constexpr int kFlowLag = 32;                                // fields between a field's x and y units
 
 struct FlowArgs {
@@ -150,9 +151,13 @@ __global__ void __launch_bounds__(256, 2)
   using C = float2;
   extern __shared__ __align__(1024) unsigned char flow_sm[];
   float4* tws = reinterpret_cast<float4*>(flow_sm + 2 * kFlowStage);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(flow_sm + 2 * kFlowStage + kFlowTws);
-  volatile int* uid = reinterpret_cast<volatile int*>(flow_sm + 2 * kFlowStage + kFlowTws + 16);
-  volatile int* last_block = reinterpret_cast<volatile int*>(flow_sm + 2 * kFlowStage + kFlowTws + 24);
+  // kt[axis][p] = (k_p, k_p^2 / (2M)): the Fourier multiplier of a line is (k^2/2 + c k)/M
+  // = fma(c/M, k, k^2/(2M)) with c = omega y (x lines) or -omega x (y lines); 1/M is exact
+  float2* kt = reinterpret_cast<float2*>(flow_sm + 2 * kFlowStage + kFlowTws);
+  unsigned char* ctl_sm = flow_sm + 2 * kFlowStage + kFlowTws + kFlowKt;
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(ctl_sm);
+  volatile int* uid = reinterpret_cast<volatile int*>(ctl_sm + 16);
+  volatile int* last_block = reinterpret_cast<volatile int*>(ctl_sm + 24);
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const int t = lane & 15, j = lane >> 4;  // thread of its line, line of the warp
   const long long total = 32LL * a.nbatch;
@@ -188,6 +193,10 @@ __global__ void __launch_bounds__(256, 2)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   dft256_twiddles(tws, a.tw);
+  for (int i = tid; i < 2 * kFM; i += blockDim.x) {
+    const float k = (i < kFM ? a.xi : a.xiy)[i & (kFM - 1)];
+    kt[i] = make_float2(k, 0.5f * k * k * invM);
+  }
   __syncthreads();
   if (tid == 0) {
     tk_next = atomicAdd(a.ctr, 1);
@@ -219,11 +228,11 @@ __global__ void __launch_bounds__(256, 2)
         sr[q] = make_float2(m * w[q].x, m * w[q].y);
       }
       dft256_row<-1>(w, row, t, tws);
-      const float yy = a.yc[16 * blk + l];
+      const float cy = om * a.yc[16 * blk + l] * invM;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float kx = a.xi[t + 16 * q];
-        w[q] = cscale(w[q], (0.5f * kx * kx + om * yy * kx) * invM);
+        const float2 k = kt[t + 16 * q];
+        w[q] = cscale(w[q], fmaf(cy, k.x, k.y));
       }
       dft256_row<+1>(w, row, t, tws);
       C* orow = a.out + fld * a.stride + (long long)(16 * blk + l) * kFM + t;
@@ -235,11 +244,11 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int q = 0; q < 16; ++q) w[q] = st[tile_cell(t + 16 * q, wp, j)];
       dft256_col<-1>(w, st, t, wp, j, tws);
-      const float xx = a.xc[16 * blk + 2 * wp + j];
+      const float cx = -om * a.xc[16 * blk + 2 * wp + j] * invM;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float ky = a.xiy[t + 16 * q];
-        w[q] = cscale(w[q], (0.5f * ky * ky - om * xx * ky) * invM);
+        const float2 k = kt[kFM + t + 16 * q];
+        w[q] = cscale(w[q], fmaf(cx, k.x, k.y));
       }
       dft256_col<+1>(w, st, t, wp, j, tws);
       __syncwarp();
