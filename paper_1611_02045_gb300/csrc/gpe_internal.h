@@ -150,6 +150,8 @@ cudaError_t launch_strided_tma(Pass pass, const PassArgs& a, cudaStream_t st, bo
 // it does not apply (E = 8, M in 64 .. 512, 16-byte aligned fields, at least
 // two units per block).
 cudaError_t launch_hx_bulk(const PassArgs& a, cudaStream_t st, bool* used);
+// C1, C3, AX of a complex64 solve through the bulk-copy pipeline (gpe_k_tma.cu).
+cudaError_t launch_xc_bulk(Pass pass, const PassArgs& a, cudaStream_t st, bool* used);
 
 // Per-group launchers (gpe_k_<prec>_<group>.cu).
 cudaError_t launch_group_f32_h(Pass pass, const PassArgs& a, cudaStream_t st);

@@ -323,6 +323,126 @@ __global__ void __launch_bounds__(512) pass_hx_bulk(PassArgs a, int second) {
   reduce_and_finish<P_HX>(a, acc);
 }
 
+// Input fields of a bulk-staged x pass of P_C or A p (solver, complex64), in
+// their order in a stage; V follows them.  The outputs are written by the
+// unit body into stage regions and stored back by bulk copies:
+//   C1: reads phi, t (H phi); writes s_hat over the t region -> s
+//   C3: reads s_hat, phi, t, r_{n-1}, p; writes P r over s_hat -> s and r_n over r_{n-1} -> r_prev
+//   AX: reads phi, s (P r), t, p; writes p_n over p -> p
+template <int ROLE> struct XcFields;
+template <> struct XcFields<P_C1> { static constexpr int n = 2; };
+template <> struct XcFields<P_C3> { static constexpr int n = 5; };
+template <> struct XcFields<P_AX> { static constexpr int n = 4; };
+
+// Global field k of role ROLE (input order above).
+template <int ROLE>
+__device__ __forceinline__ void* xc_field(const PassArgs& a, int k) {
+  if constexpr (ROLE == P_C1) return k == 0 ? const_cast<void*>(a.phi) : a.t;
+  else if constexpr (ROLE == P_C3) {
+    void* f[5] = {a.s, const_cast<void*>(a.phi), a.t, a.r_prev, a.p};
+    return f[k];
+  } else {
+    void* f[4] = {const_cast<void*>(a.phi), a.s, a.t, a.p};
+    return f[k];
+  }
+}
+
+// The x passes C1, C3 and AX of a complex64 solve through the bulk-copy
+// pipeline: persistent blocks walk units of lpb rows with two shared-memory
+// stages (the next unit's input rows land by 1D bulk copies while the current
+// one runs the unit body of the global-memory pass, pointed at the stage);
+// written fields go back by bulk copies.  Same arithmetic and reductions as
+// pass_x<float, float, float, M, ROLE, EV>.
+template <int M, int EV, int ROLE>
+__global__ void __launch_bounds__(512) pass_xc_bulk(PassArgs a) {
+  using C = float2;
+  constexpr int NF = XcFields<ROLE>::n;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ PassArgs sa[2];  // the unit body's arguments, pointed at stage s
+  if (a.solver && a.ctl->done) return;
+  const Scal S = scal_of(a.ctl, a);
+  const int lpb = a.lpb;
+  const int rows = lpb * M;
+  const size_t cb = (size_t)rows * sizeof(C), vb = (size_t)rows * sizeof(float);
+  const size_t sbytes = NF * cb + vb;
+  unsigned char* stage0 = smraw;
+  unsigned char* ex = smraw + 2 * sbytes;  // transform exchange [lpb][M + M/16]
+  const long long units = a.nblocks;
+  const unsigned bytes = (unsigned)sbytes;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int s = 0; s < 2; ++s) {
+      PassArgs b = a;
+      unsigned char* d = stage0 + s * sbytes;
+      C* reg[NF];
+      for (int k = 0; k < NF; ++k) reg[k] = reinterpret_cast<C*>(d + k * cb);
+      b.V = d + NF * cb;
+      if constexpr (ROLE == P_C1) { b.phi = reg[0]; b.t = reg[1]; b.s = reg[1]; }
+      else if constexpr (ROLE == P_C3) { b.s = reg[0]; b.phi = reg[1]; b.t = reg[2]; b.r_prev = reg[3]; b.p = reg[4]; }
+      else { b.phi = reg[0]; b.s = reg[1]; b.t = reg[2]; b.p = reg[3]; }
+      sa[s] = b;
+    }
+  }
+  __syncthreads();
+  // one thread: input rows of unit u into stage s
+  auto issue = [&](long long u, int s) {
+    unsigned char* d = stage0 + s * sbytes;
+    const long long e0 = u * rows;
+    sa[s].row0 = a.row0 + (int)(u * lpb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[s], bytes);
+    for (int k = 0; k < NF; ++k)
+      bulk_load(d + k * cb, static_cast<const C*>(xc_field<ROLE>(a, k)) + e0, (unsigned)cb, &bar[s]);
+    bulk_load(d + NF * cb, static_cast<const float*>(a.V) + e0, (unsigned)vb, &bar[s]);
+  };
+  // one thread: written regions of unit u in stage s back to global memory
+  auto store = [&](long long u, int s) {
+    unsigned char* d = stage0 + s * sbytes;
+    const long long e0 = u * rows;
+    auto put = [&](void* dst, int k) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                   ::"l"(static_cast<C*>(dst) + e0), "r"(smem_u32(d + k * cb)), "r"((unsigned)cb) : "memory");
+    };
+    if constexpr (ROLE == P_C1) put(a.s, 1);
+    else if constexpr (ROLE == P_C3) { put(a.s, 0); put(a.r_prev, 3); }
+    else put(a.p, 3);
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  };
+
+  Acc acc[kMaxMoments];
+#pragma unroll
+  for (int k = 0; k < kMaxMoments; ++k) acc[k] = Acc{0.0f, 0.0f};
+  if (threadIdx.x == 0 && (long long)blockIdx.x < units) issue(blockIdx.x, 0);
+  int i = 0;
+  for (long long u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool next = u + gridDim.x < units;
+    if (threadIdx.x == 0 && next) {
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // stage s^1 stored back (unit i-1)
+      issue(u + gridDim.x, s ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(&a.ctl->status, 6);  // GPE_ERR_TIMEOUT
+        atomicExch(&a.ctl->done, 1);
+        mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+        if (next) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      break;
+    }
+    xunit<float, float, float, M, ROLE, EV>(sa[s], S, 0, ex, acc);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // stage writes before the bulk stores
+    __syncthreads();
+    if (threadIdx.x == 0) store(u, s);
+  }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  reduce_and_finish<ROLE>(a, acc);
+}
 // Tensor map over a complex64 field [nz][ny][nx] (8-byte elements), boxes of
 // tx x-columns along the pass axis (BOX rows).
 bool encode_field(CUtensorMap* m, const void* base, const PassArgs& a, int box) {
@@ -446,6 +566,67 @@ cudaError_t launch_hx_one(const PassArgs& a0, cudaStream_t st, bool* used) {
   return cudaGetLastError();
 }
 
+template <int M, int EV, int ROLE>
+cudaError_t launch_xc_one(const PassArgs& a0, cudaStream_t st, bool* used) {
+  constexpr int Tl = LineCfg<M, EV>::Tl;
+  constexpr int NF = XcFields<ROLE>::n;
+  PassArgs a = a0;
+  // up to 256 threads per block, units of lpb whole lines; fewer lines when the
+  // two stages would not leave room for two blocks per SM
+  const long long nlines = (long long)a.ny * a.nz;
+  int lpb = 256 / Tl;
+  auto smem_of = [&](int l) {
+    return 2 * ((size_t)l * M * (NF * sizeof(float2) + sizeof(float))) + (size_t)l * (M + M / 16) * sizeof(float2);
+  };
+  while (lpb > 1 && (nlines % lpb || smem_of(lpb) > 110 * 1024)) lpb >>= 1;
+  if (nlines % lpb || smem_of(lpb) > 200 * 1024) return cudaSuccess;
+  a.lpb = lpb;
+  a.nblocks = (int)(nlines / lpb);
+  const int threads = Tl * lpb;
+  const size_t cb = (size_t)lpb * M * sizeof(float2), vb = (size_t)lpb * M * sizeof(float);
+  if ((cb & 15) || (vb & 15)) return cudaSuccess;
+  const void* ptrs[6] = {a.phi, a.t, a.s, a.r_prev, a.p, a.V};
+  for (const void* q : ptrs)
+    if (reinterpret_cast<uintptr_t>(q) & 15u) return cudaSuccess;
+  const size_t smem = smem_of(lpb);
+  auto kern = pass_xc_bulk<M, EV, ROLE>;
+  static DeviceOnce attr;
+  static std::atomic<int> occ_dev[64][8];  // [device][log2 lpb]
+  const int dev = DeviceOnce::device();
+  if (!attr.done(dev)) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr.set(dev);
+  }
+  int lg = 0;
+  while ((1 << lg) < lpb && lg < 7) ++lg;
+  int occ = (dev >= 0 && dev < 64) ? occ_dev[dev][lg].load() : 0;
+  if (occ <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess || occ < 1) { cudaGetLastError(); return cudaSuccess; }
+    if (dev >= 0 && dev < 64) occ_dev[dev][lg].store(occ);
+  }
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaGetLastError();
+  const long long grid = (long long)occ * nsm;
+  // at least two units per block, and no more blocks than the plan's (the reduction partials hold those)
+  if (a.nblocks < 2 * grid || grid > a0.nblocks) return cudaSuccess;
+  *used = true;
+  kern<<<(unsigned)grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ROLE>
+cudaError_t launch_xc_role(const PassArgs& a, cudaStream_t st, bool* used) {
+  switch (a.M) {
+    case 64: return launch_xc_one<64, 8, ROLE>(a, st, used);
+    case 128: return launch_xc_one<128, 8, ROLE>(a, st, used);
+    case 256: return launch_xc_one<256, 8, ROLE>(a, st, used);
+    case 512: return launch_xc_one<512, 8, ROLE>(a, st, used);
+    default: return cudaSuccess;
+  }
+}
+
 }  // namespace
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -492,6 +673,21 @@ cudaError_t launch_strided_tma(Pass pass, const PassArgs& a, cudaStream_t st, bo
     case P_CCORE: return launch_s_role<P_CCORE>(a, st, used);
     case P_CINV: return launch_s_role<P_CINV>(a, st, used);
     case P_AMID: return launch_s_role<P_AMID>(a, st, used);
+    default: return cudaSuccess;
+  }
+}
+
+// The x passes C1, C3 and AX of a complex64 solve through the bulk-copy
+// pipeline when the plan and the fields allow it (solver mode, E = 8,
+// M in {64, 128, 256, 512}, 16-byte aligned fields, at least two units per
+// block); *used = false otherwise (the caller launches pass_x).
+cudaError_t launch_xc_bulk(Pass pass, const PassArgs& a, cudaStream_t st, bool* used) {
+  *used = false;
+  if ((a.E != 0 && a.E != 8) || !a.solver || a.row0 != 0) return cudaSuccess;
+  switch (pass) {
+    case P_C1: return launch_xc_role<P_C1>(a, st, used);
+    case P_C3: return launch_xc_role<P_C3>(a, st, used);
+    case P_AX: return launch_xc_role<P_AX>(a, st, used);
     default: return cudaSuccess;
   }
 }

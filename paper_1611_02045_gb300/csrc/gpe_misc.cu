@@ -47,12 +47,15 @@ static cudaError_t launch_pass_e4(int mode, Pass pass, const PassArgs& a, cudaSt
 cudaError_t launch_pass(int mode, Pass pass, const PassArgs& a, cudaStream_t st) {
   if (a.E == 4) return launch_pass_e4(mode, pass, a, st);
   // complex64 passes through the TMA pipelines where the plan and the fields allow:
-  // the x pass of H phi and every strided pass (also the single-precision strided
-  // passes of the refinement phase, mode 2)
+  // the x passes (H phi; in a solve also C1, C3 and AX) and every strided pass (also
+  // the single-precision strided passes of the refinement phase, mode 2)
   const bool strided = pass == P_HMID || pass == P_CFWD || pass == P_CCORE || pass == P_CINV || pass == P_AMID;
-  if ((mode == 0 && (strided || pass == P_HX)) || (mode == 2 && strided && pass != P_HMID)) {
+  const bool xc = pass == P_C1 || pass == P_C3 || pass == P_AX;
+  if ((mode == 0 && (strided || pass == P_HX || xc)) || (mode == 2 && strided && pass != P_HMID)) {
     bool used = false;
-    const cudaError_t e = pass == P_HX ? launch_hx_bulk(a, st, &used) : launch_strided_tma(pass, a, st, &used);
+    const cudaError_t e = pass == P_HX ? launch_hx_bulk(a, st, &used)
+                          : xc        ? launch_xc_bulk(pass, a, st, &used)
+                                      : launch_strided_tma(pass, a, st, &used);
     if (e != cudaSuccess || used) return e;
   }
   if (mode == 0) return launch_pass_f32(pass, a, st);
