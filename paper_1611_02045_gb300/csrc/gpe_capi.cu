@@ -383,9 +383,13 @@ extern "C" const char* gpe_last_error(const gpe_ctx* c) { return c ? c->err.c_st
 
 // H passes on (phi, f): t = A_x f + (V + eta|phi|^2) f, then the y (and z) parts
 // accumulated; the last one writes `out` (or t) and finalises the energy terms.
-static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, void* out, Ctl* ctl) {
+// moments = false: H phi as a plain operator (gpe_apply_H); the passes skip the
+// energy moments and the scalar step that only gpe_energy and the solver read.
+static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, void* out, Ctl* ctl,
+                        bool moments = true) {
   PassArgs a = base_args(c, prec, 0, prec);
   a.ctl = ctl; a.phi = phi; a.f = f; a.t = c->pb[prec].t;
+  a.nomoments = moments ? 0 : 1;
   // fields above 64 MB (beyond L2 with the operator's other arrays): the x pass
   // prefetches the rows of the block one wave ahead (two blocks per SM)
   if ((double)c->N * (prec == 0 ? 8.0 : 16.0) > 64.0 * 1024 * 1024) a.pf = 2 * c->nsm;
@@ -393,6 +397,7 @@ static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, vo
   for (int ax = 1; ax < c->dim; ++ax) {
     PassArgs b = base_args(c, prec, ax, prec);
     b.ctl = ctl; b.phi = phi; b.f = f; b.t = c->pb[prec].t;
+    b.nomoments = a.nomoments;
     b.last_axis = (ax == c->dim - 1);
     b.out = b.last_axis ? out : nullptr;
     GPE_CU(c, launch(prec, P_HMID, b, c->st));
@@ -403,7 +408,7 @@ static gpe_status run_H(gpe_ctx* c, int prec, const void* phi, const void* f, vo
 extern "C" gpe_status gpe_apply_H(gpe_ctx* c, const void* phi, const void* f, void* out) {
   if (!c) return GPE_ERR_ARG;
   if (!phi || !f || !out) { c->err = "null field pointer"; return GPE_ERR_ARG; }
-  return run_H(c, c->work, phi, f, out, c->ctl_api);
+  return run_H(c, c->work, phi, f, out, c->ctl_api, false);
 }
 
 extern "C" gpe_status gpe_apply_H_batch(gpe_ctx* c, int nbatch, const void* phi, const void* f, void* out) {

@@ -108,6 +108,7 @@ struct PassArgs {
   int nblocks;     // grid size
   int pf;          // contiguous H pass outside a solve: L2 prefetch of the rows of unit + pf (0: none)
   int solver;      // 1: inside a solve (uses ctl scalars, solver reductions)
+  int nomoments;   // 1: the caller needs no reductions (H phi as a plain operator): passes skip them
   int last_axis;   // 1: this pass is the final one of its operator (runs the finaliser)
   double weight;   // h^d
   double eta, omega;

@@ -855,6 +855,7 @@ __device__ __forceinline__ void store_sums(const PassArgs& a, const double (&tot
 template <int ROLE>
 __device__ __forceinline__ void reduce_and_finish(const PassArgs& a, const Acc* acc) {
   constexpr int K = Moments<ROLE>::K;
+  if (a.nomoments) return;  // uniform over the launch
   if constexpr (K > 0) {
     // the P_C passes reduce only inside a solve
     if ((ROLE == P_C1 || ROLE == P_C3) && !a.solver) return;
